@@ -1,0 +1,316 @@
+"""Benchmark of the SGSPM hot path on B300: one time step of the 256x256x8 film.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+A "step" is one full SGSPM time step (Sec. 3.2: two heat solves at m^n, the forward and
+backward Gauss-Seidel sweeps with their four heat solves and stray-field refreshes, the
+damping heat flow and the projection) of a 256x256x8-cell film (h = 1/256, eps = 0.016,
+Q = 6.2e-4 along x, stray field on, alpha = 1e-3, h_e = (0.02, 0, 0), dt = 0.01) in the
+FP32 form, from a seeded smoothed random state.  Metric: cell-steps/s (cells x steps / s).
+
+Default arm: the CUDA library through its C ABI.  Every timed step starts with a cold L2
+(a 256 MiB buffer is written between steps, outside the event pair).  Under torchrun each
+rank advances its own replica film (replicas only: a film does not shard), so the
+whole-job value is the sum over ranks of cells x steps / max-over-ranks time.
+
+--impl reference: the FP64 CPU oracle (oracle/) on the host cores, same film and metric,
+each step one full oracle step; rank 0 only.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_28113_b300 import inputs  # noqa: E402
+
+WORKLOAD = "film256x256x8_fp32"
+METRIC = "SGSPM cell-steps/s (256x256x8 film, FP32 form, stray field on)"
+UNIT = "cell-steps/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax = float(r[1])
+                for n, v in zip(names, r[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(w, m0, nsteps=4):
+    """The oracle as it stands, on the host cores: FP64 numpy/scipy with all workers."""
+    from oracle import scheme
+    cores = os.cpu_count()
+    o = scheme.Oracle(scheme.Params(n=w["n"], h=w["h"], eps=w["eps"], Q=w["Q"], alpha=w["alpha"], dt=w["dt"],
+                                    u=w["u"], he=w["he"], workers=cores))
+    m = m0.copy()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        m = o.step(m, 0.0)
+    dt = time.perf_counter() - t0
+    ncell = int(np.prod(w["n"]))
+    return {"value": ncell * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} full oracle steps of the 256x256x8 film (FP64, scipy.fft workers={cores}); "
+                      f"Newell set-up excluded"}, m
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = inputs.WORKLOADS[WORKLOAD]
+    m0 = inputs.initial_state(w)
+    nsteps = max(1, args.steps)
+    from oracle import scheme
+    cores = os.cpu_count()
+    o = scheme.Oracle(scheme.Params(n=w["n"], h=w["h"], eps=w["eps"], Q=w["Q"], alpha=w["alpha"], dt=w["dt"],
+                                    u=w["u"], he=w["he"], workers=cores))
+    m = m0.copy()
+    for _ in range(args.warmup):
+        m = o.step(m, 0.0)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        m = o.step(m, 0.0)
+    dt = time.perf_counter() - t0
+    ncell = int(np.prod(w["n"]))
+    value = ncell * nsteps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": nsteps,
+            "warmup": args.warmup, "ms_per_step": dt / nsteps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": list(w["n"]), "stray": True, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{nsteps} full oracle steps after {args.warmup} warm-up steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# algorithmic bytes per cell of each launch kind, FP32 (field crossings x 4 B; see the design notes)
+def algorithmic_bytes_per_cell(kind):
+    k, v = divmod(kind, 10)
+    if k == 2:            # stray refresh operator: changed inputs read + outputs written
+        reads = 3 if v == 2 else 1
+        return 4 * (reads + v)
+    if k == 1:            # heat solve: read rhs, write solution, per field
+        return 4 * 2 * v
+    return None
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as tdist
+    from paper_2606_28113_b300 import sgspm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    w = inputs.WORKLOADS[WORKLOAD]
+    ncell = int(np.prod(w["n"]))
+    m0 = inputs.initial_state(dict(w, seed=w["seed"] + rank))
+    stream = torch.cuda.current_stream()
+    H = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
+                   stream=stream.cuda_stream)
+    m0_t = torch.from_numpy(m0.astype(np.float32).reshape(-1)).cuda()
+    H.set_m(m0_t)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    H.step(args.warmup)
+    H.sync()
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed steps, cold L2 before each step -----------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            H.step(1)
+            ev[i][1].record(stream)
+        barrier()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * ncell * args.steps / (step_ms / 1e3)
+    H.sync()
+
+    # ---- dominant kernel: per-launch device times of one step, L2 warm (inside a long run) ---
+    prof = {}
+    for _ in range(3):
+        for kind, ms in H.profile_step():
+            prof.setdefault(kind, []).append(ms)
+    share = {k: sum(v) for k, v in prof.items()}
+    total = sum(share.values())
+    kinds = {0: "xz_slab", 1: "y_heat", 2: "y_stray"}
+    per_type = {}
+    for k, t in share.items():
+        per_type.setdefault(k // 10, 0.0)
+        per_type[k // 10] += t
+    dom_type = max(per_type, key=per_type.get)
+    # roofline of the dominant launch variant of the dominant kernel
+    dom_kind = max((k for k in share if k // 10 == dom_type), key=lambda k: share[k])
+    dom_ms = float(np.mean(prof[dom_kind]))
+    bpc = algorithmic_bytes_per_cell(dom_kind)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    roof = None
+    if bpc is not None and hbm:
+        achieved = bpc * ncell / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{kinds[dom_type]} (launch kind {dom_kind})", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": bpc * ncell, "launch_ms": dom_ms,
+                "kernel_share_of_step": per_type[dom_type] / total, "traffic": None}
+    # whole-step algorithmic fraction (292 B per cell-step, FP32)
+    step_frac = 292.0 * value / world / (hbm * 1e9) if hbm else None
+
+    # ---- accuracy of the FP32 form against the FP64 form on the same GPU --------------------
+    nacc = min(args.steps, 200)
+    Ha = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
+                    stream=stream.cuda_stream)
+    Hb = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=True,
+                    stream=stream.cuda_stream)
+    Ha.set_m(m0)
+    Hb.set_m(m0)
+    Ha.step(nacc)
+    ev64 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    Hb.step(2)
+    Hb.sync()
+    ev64[0].record(stream)
+    Hb.step(nacc - 2)
+    ev64[1].record(stream)
+    Hb.sync()
+    fp64_ms = ev64[0].elapsed_time(ev64[1]) / (nacc - 2)
+    ma, mb = Ha.get_m(), Hb.get_m()
+    Ea, Eb = Ha.energy()[0], Hb.energy()[0]
+    Ha.close()
+    Hb.close()
+    max_dm = float(np.abs(ma - mb).max())
+    rel_e = float(abs(Ea[4] - Eb[4]) / abs(Eb[4]))
+
+    # ---- end to end through the C ABI with host buffers -------------------------------------
+    host_in = torch.from_numpy(m0.astype(np.float32).reshape(-1)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ne = max(3, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(ne):
+        H.set_m(host_in)
+        H.step(1)
+        H.get_m(host_out)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * ncell * ne / e2e_s
+    launches = args.steps * H.launches_per_step()
+    H.close()
+
+    if rank == 0:
+        cpu, _ = cpu_baseline(w, m0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else (None, None)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": list(w["n"]), "h": w["h"][0], "eps": w["eps"], "Q": w["Q"],
+                           "alpha": w["alpha"], "dt": w["dt"], "he": list(w["he"]), "stray": True,
+                           "parallelism": f"replicas{world}", "l2": "flushed before every timed step (256 MiB write)"},
+                "roofline": roof,
+                "step_algorithmic_hbm_frac": step_frac,
+                "fp64_form": {"ms_per_step": fp64_ms, "value": ncell / (fp64_ms / 1e3), "unit": UNIT},
+                "speedup_vs_fp64_form": (fp64_ms / (step_ms / args.steps)),
+                "accuracy_vs_fp64_form": {"steps": nacc, "max_abs_dm": max_dm, "rel_energy_err": rel_e},
+                "launch_shares": {str(k): v / total for k, v in sorted(share.items())},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * ncell * 4,
+                        "d2h_bytes_per_step": 3 * ncell * 4,
+                        "path": "sgspm_set_field(pinned host f32) + sgspm_step(1) + sgspm_get_field(pinned host f32)"},
+                "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps for cpu_baseline (0: skip)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * sgspm.h - C ABI of the B300 (sm_103a) SGSPM library `libsgspm.so`.
+ *
+ * One time step of the symmetric Gauss-Seidel projection method (SGSPM, Sec. 3.2 of
+ * the paper) for the Landau-Lifshitz-Gilbert equation (Sec. 2, Eq. (1)),
+ *     m_t = -m x h_eff - alpha m x (m x h_eff),
+ *     h_eff = eps Delta m - Q (m - (m.u)u) + h_s + h_e,
+ * on a uniform grid of nx*ny*nz rectangular cells with homogeneous Neumann boundaries
+ * (Eq. (2)).  Each step:
+ *   Step 1 (implicit symmetric Gauss-Seidel, Sec. 3.2): heat solves
+ *       g_i = (I - eps dt Delta_h)^{-1} (m_i + dt f_i),  f = -Q(m-(m.u)u) + h_s + h_e,
+ *     a forward sweep m1* -> m2* -> m3* and a backward sweep m3** -> m2** -> m1**, each
+ *     cross-product update using the newest g;
+ *   Step 2 (heat flow without constraint): (I - alpha eps dt Delta_h) m*** = m** + alpha dt f**;
+ *   Step 3 (projection): m^{n+1} = m*** / |m***|.
+ * With SGSPM_GSPM the one-sided scheme of Sec. 3.1 runs instead (forward sweep only).
+ *
+ * Discretisation (readings of what the paper leaves open):
+ *   - Delta_h is the cell-centred 7-point Laplacian with mirror ghosts, diagonalised by
+ *     DCT-II along x, y, z; the solves are done in that basis.
+ *   - h_s = -N * m is the zero-padded FFT convolution with the Newell demagnetising
+ *     tensor (cell-averaged dipole kernel), evaluated in FP64 once at create time.
+ *   - f is re-evaluated (incl. h_s) at the newest state each time a g is formed;
+ *     SGSPM_FROZEN_STRAY instead uses h_s(m^n) in Step 1 and h_s(m**) in Step 2.
+ *
+ * Memory and streams.  Fields are structure-of-arrays [3][nz][ny][nx] with x fastest.
+ * For a batch handle the fields of all films are concatenated in film order.  Every
+ * call that takes a pointer accepts host or device memory (the copy direction is
+ * resolved by unified addressing) and copies the data; the caller keeps ownership.
+ * All work is enqueued on the CUDA stream given at create time; calls that return data
+ * to the caller (get_field, energy, sync) synchronise that stream.  The library owns all
+ * of its device buffers and frees them in sgspm_destroy.  A handle must not be used
+ * from two host threads at once.
+ *
+ * Errors.  Every int-returning call returns SGSPM_OK (0) or a negative status; the text
+ * of the last error on the handle is returned by sgspm_last_error.  Device-side
+ * problems (a non-finite value or a zero vector before projection) are latched in a
+ * device status word and reported as SGSPM_ERR_NONFINITE by the next synchronising call.
+ */
+#ifndef SGSPM_H
+#define SGSPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Grid: cell counts (>= 1; 1D/2D problems use size-1 axes) and cell sizes (> 0). */
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+} sgspm_grid;
+
+typedef struct sgspm_ctx* sgspm_t;
+
+enum {
+    SGSPM_OK = 0,
+    SGSPM_ERR_ARG = -1,          /* invalid argument (checked on the host)                  */
+    SGSPM_ERR_OOM = -2,          /* device allocation failed                                */
+    SGSPM_ERR_CUDA = -3,         /* a CUDA runtime call failed                              */
+    SGSPM_ERR_NONFINITE = -4,    /* device status: non-finite value or |m***| = 0            */
+    SGSPM_ERR_TIMEOUT = -5,      /* device status: a bounded wait expired                   */
+    SGSPM_ERR_STATE = -6,        /* call not valid in the handle's current state            */
+    SGSPM_ERR_UNSUPPORTED = -7   /* size not supported (axis length factors other than 2,3,5,
+                                    or a slab that does not fit in shared memory)          */
+};
+
+/* create flags */
+enum {
+    SGSPM_FP64 = 1 << 0,          /* all arithmetic in FP64 (default: FP32 bulk arithmetic)   */
+    SGSPM_GSPM = 1 << 1,          /* one-sided GSPM of Sec. 3.1 instead of SGSPM (Sec. 3.2)   */
+    SGSPM_NO_STRAY = 1 << 2,      /* h_s = 0                                                 */
+    SGSPM_FROZEN_STRAY = 1 << 3,  /* h_s(m^n) for Step 1 and h_s(m**) for Step 2             */
+    SGSPM_NO_GRAPH = 1 << 4       /* launch kernels directly instead of a captured CUDA graph */
+};
+
+/* field selectors */
+enum {
+    SGSPM_M = 0,      /* magnetisation m (set: normalised on the device; get: current m)      */
+    SGSPM_HE = 1,     /* per-cell applied field h_e (set only; replaces the uniform field)    */
+    SGSPM_HS = 2      /* stray field h_s(m) of the current m (get only; computed on demand)   */
+};
+
+/* dtypes of caller buffers */
+enum { SGSPM_F32 = 0, SGSPM_F64_DATA = 1 };
+
+/* forcing kinds for sgspm_set_forcing: the manufactured solutions of Sec. 5.1 on [0,1]^d */
+enum { SGSPM_FORCE_NONE = 0, SGSPM_FORCE_MMS_1D = 1, SGSPM_FORCE_MMS_3D = 3 };
+
+/*
+ * sgspm_create - one film.  eps (exchange), Q (anisotropy), alpha (damping) >= 0, dt > 0,
+ * easy_axis != 0 (normalised internally).  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream).  Allocates the device state, evaluates the Newell tensor and its
+ * padded spectrum in FP64 on the device, and builds the FFT plans.  m starts undefined:
+ * call sgspm_set_field(SGSPM_M) before stepping.  On error *out is left NULL.
+ */
+int sgspm_create(const sgspm_grid* grid, double eps, double Q, double alpha, double dt,
+                 const double easy_axis[3], int flags, void* cuda_stream, sgspm_t* out);
+
+/*
+ * sgspm_create_batch - nfilm independent films (sizes may differ) advanced together:
+ * every pass of a step is one kernel launch over all films.  Parameter arrays have
+ * nfilm entries (easy_axis: 3*nfilm).  Flags apply to all films.
+ */
+int sgspm_create_batch(int nfilm, const sgspm_grid* grids, const double* eps, const double* Q,
+                       const double* alpha, const double* dt, const double* easy_axis,
+                       int flags, void* cuda_stream, sgspm_t* out);
+
+/* Uniform applied field per film (3*nfilm doubles); clears any per-cell h_e. */
+int sgspm_set_applied_field(sgspm_t h, const double* he);
+
+/* Copy a field in (SGSPM_M, SGSPM_HE).  ptr: host or device, layout as above, dtype F32/F64. */
+int sgspm_set_field(sgspm_t h, int which, const void* ptr, int dtype);
+
+/* Copy a field out (SGSPM_M, SGSPM_HS) into host or device memory; synchronises. */
+int sgspm_get_field(sgspm_t h, int which, void* ptr, int dtype);
+
+/* Enqueue n >= 1 time steps on the handle's stream (asynchronous). */
+int sgspm_step(sgspm_t h, long long n);
+
+/*
+ * Discrete energy of the current m, FP64, per film: out[5*f + {0..4}] =
+ * {exchange, anisotropy, stray, zeeman, total} with
+ *   exchange = V eps/2 sum_faces |m_c - m_c'|^2 / h^2,  anisotropy = V Q/2 sum (|m|^2 - (m.u)^2),
+ *   stray = -V/2 sum h_s.m,  zeeman = -V sum h_e.m,  V = hx hy hz
+ * (the normalisation for which h_eff = -(1/V) dE/dm; Sec. 2 prints E without the 1/2).
+ * Synchronises.
+ */
+int sgspm_energy(sgspm_t h, double* out);
+
+/* Manufactured forcing of Sec. 5.1: m*** += dt f_e(x, t_n) before projection. */
+int sgspm_set_forcing(sgspm_t h, int kind);
+
+/* Simulation time t (per film t = t0 + steps*dt); set resets the step counter. */
+int sgspm_set_time(sgspm_t h, double t);
+int sgspm_get_time(sgspm_t h, double* t);
+
+/* Wait for all enqueued work and report the latched device status. */
+int sgspm_sync(sgspm_t h);
+
+/* Release every device buffer and the handle (NULL is a no-op). */
+int sgspm_destroy(sgspm_t h);
+
+/* Text of the last error on h (or of the last failed create when h is NULL). */
+const char* sgspm_last_error(sgspm_t h);
+
+/*
+ * Run ONE time step with a CUDA event between consecutive kernel launches (no graph) and
+ * report each launch's device time: ms[i] (milliseconds) and kind[i] = 10*k + v, with
+ * k = 0 slab (XZ) pass (v = 1 right-hand sides, 2 Gauss-Seidel update, 3 projection),
+ * k = 1 heat-solve line pass and k = 2 stray-field line pass (v = fields / outputs).
+ * cap is the capacity of both arrays (>= sgspm_launches_per_step).  Returns the number of
+ * launches (>= 0) or a negative status.  The step advances the state like sgspm_step(1).
+ */
+int sgspm_profile_step(sgspm_t h, float* ms, int* kind, int cap);
+
+/* Number of kernel launches one sgspm_step(1) enqueues (for launch accounting). */
+int sgspm_launches_per_step(sgspm_t h);
+
+/* ABI version (major*100 + minor). */
+int sgspm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGSPM_H */

@@ -1,0 +1,1050 @@
+// C ABI of libsgspm.so: handle lifetime, set-up (plans, twiddles, Newell spectrum), the
+// per-step pass programs and their CUDA-graph capture.  See include/sgspm.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sgspm.h"
+#include "common.cuh"
+#include "passes.cuh"
+#include "passes.cu"
+#include "newell.cu"
+
+namespace sgspm {
+
+// real field slots
+enum { M1 = 0, M2, M3, A1, A2, A3, B1, B2, E3N, E1S, E3SS, D1, D2, D3, HS1, HS2, HS3, NSLOT };
+// spectral slots
+enum { S1 = 0, S2, S3, H1, H2, H3, NSPEC };
+
+struct Launch {
+    int kind;   // 0 xz, 1 y heat, 2 y stray, 3 step counter
+    XZProg xz;
+    YProg y;
+};
+
+}  // namespace sgspm
+
+using namespace sgspm;
+
+struct sgspm_ctx {
+    int nfilm = 0;
+    int flags = 0;
+    bool fp64 = false;
+    bool stray = true;
+    cudaStream_t stream = nullptr;     // caller's stream
+    cudaStream_t cap = nullptr;        // private capture stream
+    std::vector<Film> films;
+    std::vector<Plan> plans;
+    std::map<int, int> plan_of;
+    long long ncell = 0, nspec = 0, nktab = 0;
+    size_t tsz = 4;
+    // device
+    Film* d_films = nullptr;
+    Plan* d_plans = nullptr;
+    void* d_tw = nullptr;
+    void* d_lam = nullptr;
+    void* d_ktab = nullptr;
+    void* d_field[NSLOT] = {};
+    void* d_spec[NSPEC] = {};
+    void* d_he = nullptr;
+    bool he_cell = false;
+    int* d_status = nullptr;
+    long long* d_step = nullptr;
+    void* d_stage = nullptr;
+    int4* d_work_xz = nullptr;
+    int n_xz = 0;
+    int4* d_work_yh = nullptr;
+    int n_yh = 0;
+    int tx_h = 8;
+    int4* d_work_ys[4] = {};
+    int n_ys[4] = {};
+    int tx_s[4] = {};
+    size_t smem_xz = 0, smem_yh = 0, smem_ys[4] = {};
+    int4* d_work_e = nullptr;
+    int n_e = 0;
+    int* d_first_e = nullptr;
+    double* d_epart = nullptr;
+    double* d_eout = nullptr;
+    std::vector<Launch> step_prog, hs_prog, fwd_prog;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool have_m = false;
+    bool forcing = false;
+    long long steps = 0;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+            return e_ == cudaErrorMemoryAllocation ? SGSPM_ERR_OOM : SGSPM_ERR_CUDA;           \
+        }                                                                                      \
+    } while (0)
+
+static int fail(sgspm_ctx* ctx, int code, const std::string& msg) {
+    ctx->err = msg;
+    return code;
+}
+
+// ---------------------------------------------------------------------------------------------
+// host numerics: twiddles (long double), Gauss-Legendre rules, radix plans
+// ---------------------------------------------------------------------------------------------
+static void cis(long long m, long long P, double* c, double* s) {
+    // cos, sin of 2 pi m / P, evaluated in long double and rounded once
+    long long r = ((m % P) + P) % P;
+    long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)r / (long double)P;
+    *c = (double)cosl(th);
+    *s = (double)sinl(th);
+}
+
+static bool factor(int P, std::vector<int>& rs) {
+    rs.clear();
+    int p = P;
+    const int order[5] = {8, 4, 2, 3, 5};
+    for (int r : order)
+        while (p % r == 0) {
+            rs.push_back(r);
+            p /= r;
+        }
+    return p == 1 && (int)rs.size() <= kMaxStages;
+}
+
+static void gauss_legendre(int q, double* x, double* w) {
+    for (int i = 0; i < q; ++i) {
+        long double z = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (q + 0.5L));
+        long double pp = 0;
+        for (int it = 0; it < 100; ++it) {
+            long double p1 = 1, p2 = 0;
+            for (int j = 1; j <= q; ++j) {
+                long double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0L * j - 1.0L) * z * p2 - (j - 1.0L) * p3) / j;
+            }
+            pp = q * (z * p1 - p2) / (z * z - 1.0L);
+            long double z1 = z;
+            z = z1 - p1 / pp;
+            if (fabsl(z - z1) < 1e-19L) break;
+        }
+        x[i] = (double)(-z);
+        w[i] = (double)(2.0L / ((1.0L - z * z) * pp * pp));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+static Dev<T> dev_view(sgspm_ctx* ctx) {
+    Dev<T> d;
+    d.films = ctx->d_films;
+    d.plans = ctx->d_plans;
+    d.tw = (const cplx<T>*)ctx->d_tw;
+    d.lam = (const T*)ctx->d_lam;
+    d.ktab = (const T*)ctx->d_ktab;
+    for (int i = 0; i < kMaxSlots; ++i) d.field[i] = i < NSLOT ? (T*)ctx->d_field[i] : nullptr;
+    for (int i = 0; i < kMaxSpec; ++i) d.spec[i] = i < NSPEC ? (cplx<T>*)ctx->d_spec[i] : nullptr;
+    d.he_cell = ctx->he_cell ? (const T*)ctx->d_he : nullptr;
+    d.status = ctx->d_status;
+    d.step_ctr = ctx->d_step;
+    return d;
+}
+
+template <typename T>
+static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
+    Dev<T> d = dev_view<T>(ctx);
+    switch (L.kind) {
+        case 0:
+            xz_kernel<T><<<ctx->n_xz, kThreads, ctx->smem_xz, st>>>(d, ctx->d_work_xz, L.xz, ctx->stray ? 1 : 0);
+            break;
+        case 1:
+            y_heat_kernel<T><<<ctx->n_yh, kThreads, ctx->smem_yh, st>>>(d, ctx->d_work_yh, L.y);
+            break;
+        case 2: {
+            int n = L.y.n;
+            y_stray_kernel<T><<<ctx->n_ys[n], kThreads, ctx->smem_ys[n], st>>>(d, ctx->d_work_ys[n], L.y, ctx->tx_s[n]);
+            break;
+        }
+        default:
+            step_counter_kernel<<<1, 1, 0, st>>>(ctx->d_step);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SGSPM_OK;
+}
+
+static int enqueue(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
+    return ctx->fp64 ? enqueue_t<double>(ctx, L, st) : enqueue_t<float>(ctx, L, st);
+}
+
+static int run_prog(sgspm_ctx* ctx, const std::vector<Launch>& prog, cudaStream_t st) {
+    for (const Launch& L : prog) {
+        int rc = enqueue(ctx, L, st);
+        if (rc) return rc;
+    }
+    return SGSPM_OK;
+}
+
+// ---- program builders --------------------------------------------------------------------------
+static XZProg xz_empty() {
+    XZProg p;
+    memset(&p, 0, sizeof(p));
+    for (int i = 0; i < 3; ++i) {
+        p.rhs_h[i] = -1;
+        p.rhs_hs_store[i] = -1;
+        p.inv_store[i] = -1;
+    }
+    p.rhs_dct = 1;
+    return p;
+}
+
+static Launch mk_ystray(const std::vector<int>& outs) {
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.kind = 2;
+    L.y.kind = 1;
+    L.y.n = (int)outs.size();
+    for (int i = 0; i < 3; ++i) L.y.in_spec[i] = S1 + i;
+    for (size_t o = 0; o < outs.size(); ++o) {
+        L.y.slot[o] = outs[o];
+        L.y.out_spec[o] = H1 + outs[o];
+    }
+    return L;
+}
+
+static Launch mk_rhs(const sgspm_ctx* ctx, const std::vector<int>& comps, int s0, int s1, int s2, int damp) {
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.kind = 0;
+    L.xz = xz_empty();
+    L.xz.n_rhs = (int)comps.size();
+    for (size_t i = 0; i < comps.size(); ++i) {
+        L.xz.rhs_comp[i] = comps[i];
+        L.xz.rhs_h[i] = ctx->stray ? H1 + comps[i] : -1;
+        L.xz.rhs_out[i] = D1 + comps[i];
+    }
+    L.xz.state[0] = s0;
+    L.xz.state[1] = s1;
+    L.xz.state[2] = s2;
+    L.xz.damp = damp;
+    return L;
+}
+
+static Launch mk_yheat(const std::vector<int>& comps, int damp) {
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.kind = 1;
+    L.y.kind = 0;
+    L.y.n = (int)comps.size();
+    for (size_t i = 0; i < comps.size(); ++i) L.y.slot[i] = D1 + comps[i];
+    L.y.damp = damp;
+    return L;
+}
+
+static int slab(int i) { return -1 - i; }
+
+// Gauss-Seidel update pass: inverse-DCT of D_{comp} (delta in slab 0, optionally stored),
+// out = base + p*q - r*s, then the forward padded FFT of `out` into S_{fwd_comp}.
+static Launch mk_gs(const sgspm_ctx* ctx, int comp, int store, int out, int base, int p, int q, int r, int s, int fwd_comp) {
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.kind = 0;
+    L.xz = xz_empty();
+    L.xz.n_inv = 1;
+    L.xz.inv_in[0] = D1 + comp;
+    L.xz.inv_store[0] = store;
+    L.xz.op = 1;
+    L.xz.gs_out = out;
+    L.xz.gs_base = base;
+    L.xz.gs_p = p;
+    L.xz.gs_q = q;
+    L.xz.gs_r = r;
+    L.xz.gs_s = s;
+    if (ctx->stray && fwd_comp >= 0) {
+        L.xz.n_fwd = 1;
+        L.xz.fwd_src[0] = slab(2);
+        L.xz.fwd_dst[0] = S1 + fwd_comp;
+    }
+    return L;
+}
+
+static Launch mk_final(const sgspm_ctx* ctx, int i0, int i1, int i2) {
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.kind = 0;
+    L.xz = xz_empty();
+    L.xz.n_inv = 3;
+    for (int i = 0; i < 3; ++i) {
+        L.xz.inv_in[i] = D1 + i;
+        L.xz.fin_out[i] = M1 + i;
+    }
+    L.xz.fin_in[0] = i0;
+    L.xz.fin_in[1] = i1;
+    L.xz.fin_in[2] = i2;
+    L.xz.op = 2;
+    if (ctx->stray) {
+        L.xz.n_fwd = 3;
+        for (int i = 0; i < 3; ++i) {
+            L.xz.fwd_src[i] = slab(i);
+            L.xz.fwd_dst[i] = S1 + i;
+        }
+    }
+    return L;
+}
+
+static void build_programs(sgspm_ctx* ctx) {
+    const bool R2 = (ctx->flags & SGSPM_FROZEN_STRAY) && ctx->stray;
+    const bool gspm = (ctx->flags & SGSPM_GSPM) != 0;
+    const bool st = ctx->stray;
+    std::vector<Launch>& P = ctx->step_prog;
+    P.clear();
+    // components: 0 = paper's m1, 1 = m2, 2 = m3.  delta_i = g_i - m_i (see DESIGN: delta form)
+    // h_s at m^n, then g2^n, g3^n
+    if (st) P.push_back(mk_ystray(R2 ? std::vector<int>{0, 1, 2} : std::vector<int>{1, 2}));
+    P.push_back(mk_rhs(ctx, {1, 2}, M1, M2, M3, 0));
+    P.push_back(mk_yheat({1, 2}, 0));
+    {
+        // m1* = m1 + d2n m3 - d3n m2   (d2n in slab 0, d3n in slab 1, stored)
+        Launch L = mk_gs(ctx, 1, -1, A1, M1, slab(0), M3, slab(1), M2, R2 ? -1 : 0);
+        L.xz.n_inv = 2;
+        L.xz.inv_in[0] = D2;
+        L.xz.inv_in[1] = D3;
+        L.xz.inv_store[0] = -1;
+        L.xz.inv_store[1] = E3N;
+        P.push_back(L);
+    }
+    auto refresh = [&](int comp) {
+        if (st && !R2) P.push_back(mk_ystray({comp}));
+    };
+    // g1* at (m1*, m2, m3) -> m2* = m2 + d3n m1* - d1* m3
+    refresh(0);
+    P.push_back(mk_rhs(ctx, {0}, A1, M2, M3, 0));
+    P.push_back(mk_yheat({0}, 0));
+    P.push_back(mk_gs(ctx, 0, E1S, A2, M2, E3N, A1, slab(0), M3, R2 ? -1 : 1));
+    // g2* at (m1*, m2*, m3) -> m3* = m3 + d1* m2* - d2* m1*
+    refresh(1);
+    P.push_back(mk_rhs(ctx, {1}, A1, A2, M3, 0));
+    P.push_back(mk_yheat({1}, 0));
+    int m1f = A1, m2f = A2, m3f = A3;
+    if (!gspm) {
+        P.push_back(mk_gs(ctx, 1, -1, A3, M3, E1S, A2, slab(0), A1, R2 ? -1 : 2));
+        // backward sweep: g3** at (m1*, m2*, m3**) -> m2** = m2 + d3** m1* - d1* m3**
+        refresh(2);
+        P.push_back(mk_rhs(ctx, {2}, A1, A2, A3, 0));
+        P.push_back(mk_yheat({2}, 0));
+        P.push_back(mk_gs(ctx, 2, E3SS, B2, M2, slab(0), A1, E1S, A3, R2 ? -1 : 1));
+        // g2** at (m1*, m2**, m3**) -> m1** = m1 + d2** m3** - d3** m2**
+        refresh(1);
+        P.push_back(mk_rhs(ctx, {1}, A1, B2, A3, 0));
+        P.push_back(mk_yheat({1}, 0));
+        Launch L = mk_gs(ctx, 1, -1, B1, M1, slab(0), A3, E3SS, B2, R2 ? -1 : 0);
+        if (R2) {
+            L.xz.n_fwd = 3;
+            L.xz.fwd_src[0] = slab(2);
+            L.xz.fwd_dst[0] = S1;
+            L.xz.fwd_src[1] = B2;
+            L.xz.fwd_dst[1] = S2;
+            L.xz.fwd_src[2] = A3;
+            L.xz.fwd_dst[2] = S3;
+        }
+        P.push_back(L);
+        m1f = B1;
+        m2f = B2;
+        m3f = A3;
+    } else {
+        Launch L = mk_gs(ctx, 1, -1, A3, M3, E1S, A2, slab(0), A1, R2 ? -1 : 2);
+        if (R2) {
+            L.xz.n_fwd = 3;
+            L.xz.fwd_src[0] = A1;
+            L.xz.fwd_dst[0] = S1;
+            L.xz.fwd_src[1] = A2;
+            L.xz.fwd_dst[1] = S2;
+            L.xz.fwd_src[2] = slab(2);
+            L.xz.fwd_dst[2] = S3;
+            // slab 2 must be consumed before the global loads reuse slab 0: order it first
+            std::swap(L.xz.fwd_src[0], L.xz.fwd_src[2]);
+            std::swap(L.xz.fwd_dst[0], L.xz.fwd_dst[2]);
+        }
+        P.push_back(L);
+    }
+    // Step 2: damping heat flow at m**, Step 3: projection
+    if (st) P.push_back(mk_ystray({0, 1, 2}));
+    P.push_back(mk_rhs(ctx, {0, 1, 2}, m1f, m2f, m3f, 1));
+    P.push_back(mk_yheat({0, 1, 2}, 1));
+    P.push_back(mk_final(ctx, m1f, m2f, m3f));
+    if (ctx->forcing) {
+        Launch L;
+        memset(&L, 0, sizeof(L));
+        L.kind = 3;
+        P.push_back(L);
+    }
+
+    // h_s of the current m into HS1..3
+    ctx->hs_prog.clear();
+    if (st) {
+        ctx->hs_prog.push_back(mk_ystray({0, 1, 2}));
+        Launch L;
+        memset(&L, 0, sizeof(L));
+        L.kind = 0;
+        L.xz = xz_empty();
+        L.xz.n_rhs = 3;
+        L.xz.rhs_dct = 0;
+        for (int i = 0; i < 3; ++i) {
+            L.xz.rhs_comp[i] = i;
+            L.xz.rhs_h[i] = H1 + i;
+            L.xz.rhs_hs_store[i] = HS1 + i;
+        }
+        L.xz.state[0] = M1;
+        L.xz.state[1] = M2;
+        L.xz.state[2] = M3;
+        ctx->hs_prog.push_back(L);
+    }
+    // forward padded FFT of M1..3 into S1..3 (after set_field)
+    ctx->fwd_prog.clear();
+    if (st) {
+        Launch L;
+        memset(&L, 0, sizeof(L));
+        L.kind = 0;
+        L.xz = xz_empty();
+        L.xz.n_fwd = 3;
+        for (int i = 0; i < 3; ++i) {
+            L.xz.fwd_src[i] = M1 + i;
+            L.xz.fwd_dst[i] = S1 + i;
+        }
+        ctx->fwd_prog.push_back(L);
+    }
+}
+
+static int drop_graph(sgspm_ctx* ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    return SGSPM_OK;
+}
+
+static int capture_step(sgspm_ctx* ctx) {
+    drop_graph(ctx);
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = run_prog(ctx, ctx->step_prog, ctx->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    ctx->graph = g;
+    CK(cudaGraphInstantiate(&ctx->gexec, g, 0));
+    return SGSPM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// set-up
+// ---------------------------------------------------------------------------------------------
+static int get_plan(sgspm_ctx* ctx, int P, std::vector<double2>& tw) {
+    auto it = ctx->plan_of.find(P);
+    if (it != ctx->plan_of.end()) return it->second;
+    Plan pl;
+    memset(&pl, 0, sizeof(pl));
+    std::vector<int> rs;
+    if (!factor(P, rs)) return -1;
+    pl.P = P;
+    pl.nst = (int)rs.size();
+    for (size_t i = 0; i < rs.size(); ++i) pl.radix[i] = rs[i];
+    pl.tw = (int)tw.size();
+    for (int m = 0; m < P; ++m) {
+        double c, s;
+        cis(m, P, &c, &s);
+        tw.push_back(make_double2(c, -s));
+    }
+    pl.tw4 = (int)tw.size();
+    for (int k = 0; k < P; ++k) {
+        double c, s;
+        cis(k, 4LL * P, &c, &s);
+        tw.push_back(make_double2(c, -s));
+    }
+    int id = (int)ctx->plans.size();
+    ctx->plans.push_back(pl);
+    ctx->plan_of[P] = id;
+    return id;
+}
+
+template <typename T>
+static int upload_tw(sgspm_ctx* ctx, const std::vector<double2>& tw) {
+    std::vector<cplx<T>> v(tw.size());
+    for (size_t i = 0; i < tw.size(); ++i) {
+        v[i].x = (T)tw[i].x;
+        v[i].y = (T)tw[i].y;
+    }
+    CK(cudaMalloc(&ctx->d_tw, v.size() * sizeof(cplx<T>)));
+    CK(cudaMemcpy(ctx->d_tw, v.data(), v.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+    return SGSPM_OK;
+}
+
+template <typename T>
+static int upload_vec(sgspm_ctx* ctx, void** dst, const std::vector<double>& src) {
+    std::vector<T> v(src.begin(), src.end());
+    CK(cudaMalloc(dst, v.size() * sizeof(T) + 16));
+    CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SGSPM_OK;
+}
+
+// Newell spectrum of one film into ktab (+ off_ktab), FP64 on the device.
+template <typename T>
+static int newell_setup(sgspm_ctx* ctx, const Film& F) {
+    const int nx = F.nx, ny = F.ny, nz = F.nz, Kx = F.Kx;
+    const int Hy = F.Py / 2 + 1, Hz = F.Pz / 2 + 1;
+    const long long noct = (long long)nx * ny * nz;
+    GLTable gl;
+    memset(&gl, 0, sizeof(gl));
+    int off = 0;
+    for (int q : {4, 5, 6, 7, 8, 14}) {
+        gl.off[q] = off;
+        gauss_legendre(q, gl.x + off, gl.w + off);
+        off += q;
+    }
+    double *oct = nullptr, *A = nullptr, *B = nullptr, *C = nullptr, *tabs = nullptr;
+    const long long nA = 6LL * nz * ny * Kx, nB = 6LL * nz * Hy * Kx, nC = 6LL * Hz * Hy * Kx;
+    std::vector<double> h_tab;
+    int Ps[3] = {F.Px, F.Py, F.Pz};
+    long long toff[3];
+    for (int a = 0; a < 3; ++a) {
+        toff[a] = (long long)h_tab.size();
+        for (int m = 0; m < Ps[a]; ++m) {
+            double c, s;
+            cis(m, Ps[a], &c, &s);
+            h_tab.push_back(c);
+        }
+        for (int m = 0; m < Ps[a]; ++m) {
+            double c, s;
+            cis(m, Ps[a], &c, &s);
+            h_tab.push_back(s);
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    auto al = [&](double** p, long long n) {
+        if (e == cudaSuccess) e = cudaMalloc(p, (size_t)n * sizeof(double));
+    };
+    al(&oct, 6 * noct);
+    al(&A, nA);
+    al(&B, nB);
+    al(&C, nC);
+    al(&tabs, (long long)h_tab.size());
+    if (e == cudaSuccess) e = cudaMemcpy(tabs, h_tab.data(), h_tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        newell_octant_kernel<<<(unsigned)((noct + 127) / 128), 128>>>(oct, nx, ny, nz, F.hx, F.hy, F.hz, gl);
+        e = cudaGetLastError();
+    }
+    auto cs = [&](int a) { return tabs + toff[a]; };
+    auto sn = [&](int a) { return tabs + toff[a] + Ps[a]; };
+    if (e == cudaSuccess) {
+        newell_axis_kernel<<<(unsigned)((nA + 255) / 256), 256>>>(oct, A, 0, nx, Kx, F.Px, ny, nz, 1, nx, (long long)ny * nx,
+                                                                 noct, 1, Kx, (long long)ny * Kx, (long long)nz * ny * Kx, cs(0), sn(0));
+        newell_axis_kernel<<<(unsigned)((nB + 255) / 256), 256>>>(A, B, 1, ny, Hy, F.Py, Kx, nz, Kx, 1, (long long)ny * Kx,
+                                                                 (long long)nz * ny * Kx, Kx, 1, (long long)Hy * Kx,
+                                                                 (long long)nz * Hy * Kx, cs(1), sn(1));
+        newell_axis_kernel<<<(unsigned)((nC + 255) / 256), 256>>>(B, C, 2, nz, Hz, F.Pz, Hy * Kx, 1, (long long)Hy * Kx, 1, 0,
+                                                                 (long long)nz * Hy * Kx, (long long)Hy * Kx, 1, 0,
+                                                                 (long long)Hz * Hy * Kx, cs(2), sn(2));
+        newell_finish_kernel<T><<<(unsigned)((nC + 255) / 256), 256>>>(C, (T*)ctx->d_ktab + F.off_ktab, nC / 6,
+                                                                       1.0 / ((double)F.Px * F.Py * F.Pz));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(oct);
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(C);
+    cudaFree(tabs);
+    if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("Newell set-up: ") + cudaGetErrorString(e));
+    return SGSPM_OK;
+}
+
+template <typename T>
+static int setup_t(sgspm_ctx* ctx) {
+    const size_t V = sizeof(cplx<T>);
+    std::vector<double2> tw;
+    std::vector<double> lam;
+    // plans, offsets
+    long long oc = 0, os = 0, ok = 0;
+    std::map<std::vector<double>, long long> ktab_of;
+    std::vector<int> ktab_owner;   // film that computes each unique table (or -1)
+    for (int f = 0; f < ctx->nfilm; ++f) {
+        Film& F = ctx->films[f];
+        F.Px = F.nx > 1 ? 2 * F.nx : 1;
+        F.Py = F.ny > 1 ? 2 * F.ny : 1;
+        F.Pz = F.nz > 1 ? 2 * F.nz : 1;
+        F.Kx = F.Px / 2 + 1;
+        int ids[6] = {get_plan(ctx, F.nx, tw), get_plan(ctx, F.ny, tw), get_plan(ctx, F.nz, tw),
+                      get_plan(ctx, F.Px, tw), get_plan(ctx, F.Py, tw), get_plan(ctx, F.Pz, tw)};
+        for (int i = 0; i < 6; ++i)
+            if (ids[i] < 0)
+                return fail(ctx, SGSPM_ERR_UNSUPPORTED, "axis length has a prime factor other than 2, 3, 5 (film " + std::to_string(f) + ")");
+        F.plan_dx = ids[0];
+        F.plan_dy = ids[1];
+        F.plan_dz = ids[2];
+        F.plan_px = ids[3];
+        F.plan_py = ids[4];
+        F.plan_pz = ids[5];
+        F.off_cell = oc;
+        oc += (long long)F.nx * F.ny * F.nz;
+        F.off_spec = os;
+        os += (long long)F.Kx * F.ny * F.Pz;
+        F.lam = (int)lam.size();
+        const int ns[3] = {F.nx, F.ny, F.nz};
+        const double hs[3] = {F.hx, F.hy, F.hz};
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < ns[a]; ++k) {
+                double c, s;
+                cis(k, 4LL * ns[a], &c, &s);   // sin(pi k / (2 n))
+                lam.push_back(4.0 / (hs[a] * hs[a]) * s * s);
+            }
+        if (ctx->stray) {
+            std::vector<double> key = {(double)F.nx, (double)F.ny, (double)F.nz, F.hx, F.hy, F.hz};
+            auto it = ktab_of.find(key);
+            if (it == ktab_of.end()) {
+                F.off_ktab = ok;
+                ktab_of[key] = ok;
+                ok += 6LL * (F.Pz / 2 + 1) * (F.Py / 2 + 1) * F.Kx;
+                ktab_owner.push_back(f);
+            } else {
+                F.off_ktab = it->second;
+            }
+        }
+    }
+    ctx->ncell = oc;
+    ctx->nspec = os;
+    ctx->nktab = ok;
+    // shared-memory budgets
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int smem_max = 0;
+    CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    size_t sx = 0, sy = 0;
+    int maxPy = 1, maxny = 1;
+    for (const Film& F : ctx->films) {
+        XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray);
+        size_t b = xz_smem_bytes<T>(L);
+        if (b > sx) sx = b;
+        if (F.Py > maxPy) maxPy = F.Py;
+        if (F.ny > maxny) maxny = F.ny;
+    }
+    ctx->tx_h = 8;
+    sy = (size_t)2 * ((ctx->tx_h + 1) / 2) * maxny * V + (size_t)ctx->tx_h * maxny * sizeof(T);
+    if (sx > (size_t)smem_max || sy > (size_t)smem_max)
+        return fail(ctx, SGSPM_ERR_UNSUPPORTED, "slab of " + std::to_string(sx) + " B does not fit in shared memory");
+    ctx->smem_xz = sx;
+    ctx->smem_yh = sy;
+    for (int n = 1; n <= 3; ++n) {
+        const size_t budget = 100 * 1024;
+        int tx = (int)(budget / ((2 + n) * (size_t)maxPy * V));
+        if (tx > 16) tx = 16;
+        if (tx < 1) tx = 1;
+        ctx->tx_s[n] = tx;
+        ctx->smem_ys[n] = (size_t)(2 + n) * tx * maxPy * V;
+        if (ctx->smem_ys[n] > (size_t)smem_max)
+            return fail(ctx, SGSPM_ERR_UNSUPPORTED, "y line of length " + std::to_string(maxPy) + " does not fit in shared memory");
+    }
+    CK(cudaFuncSetAttribute(xz_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_xz));
+    CK(cudaFuncSetAttribute(y_heat_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yh));
+    CK(cudaFuncSetAttribute(y_stray_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)std::max(ctx->smem_ys[1], std::max(ctx->smem_ys[2], ctx->smem_ys[3]))));
+    // work lists
+    std::vector<int4> wx, wy, we;
+    std::vector<int> first_e;
+    for (int f = 0; f < ctx->nfilm; ++f) {
+        const Film& F = ctx->films[f];
+        for (int y = 0; y < F.ny; ++y) wx.push_back(make_int4(f, y, 0, 0));
+        for (int kz = 0; kz < F.nz; ++kz)
+            for (int x0 = 0; x0 < F.nx; x0 += ctx->tx_h) wy.push_back(make_int4(f, kz, x0, std::min(ctx->tx_h, F.nx - x0)));
+        first_e.push_back((int)we.size());
+        long long nc = (long long)F.nx * F.ny * F.nz;
+        for (long long c0 = 0; c0 < nc; c0 += 4096) we.push_back(make_int4(f, (int)c0, (int)std::min(4096LL, nc - c0), 0));
+    }
+    first_e.push_back((int)we.size());
+    auto up4 = [&](int4** d, const std::vector<int4>& h) -> int {
+        CK(cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(int4)));
+        if (!h.empty()) CK(cudaMemcpy(*d, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        return SGSPM_OK;
+    };
+    int rc;
+    if ((rc = up4(&ctx->d_work_xz, wx))) return rc;
+    if ((rc = up4(&ctx->d_work_yh, wy))) return rc;
+    if ((rc = up4(&ctx->d_work_e, we))) return rc;
+    ctx->n_xz = (int)wx.size();
+    ctx->n_yh = (int)wy.size();
+    ctx->n_e = (int)we.size();
+    for (int n = 1; n <= 3; ++n) {
+        std::vector<int4> ws;
+        for (int f = 0; f < ctx->nfilm; ++f) {
+            const Film& F = ctx->films[f];
+            for (int kz = 0; kz < F.Pz; ++kz)
+                for (int x0 = 0; x0 < F.Kx; x0 += ctx->tx_s[n]) ws.push_back(make_int4(f, kz, x0, std::min(ctx->tx_s[n], F.Kx - x0)));
+        }
+        if ((rc = up4(&ctx->d_work_ys[n], ws))) return rc;
+        ctx->n_ys[n] = (int)ws.size();
+    }
+    CK(cudaMalloc(&ctx->d_first_e, first_e.size() * sizeof(int)));
+    CK(cudaMemcpy(ctx->d_first_e, first_e.data(), first_e.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_epart, std::max(1, ctx->n_e) * 4 * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_eout, ctx->nfilm * 5 * sizeof(double)));
+    // tables
+    if ((rc = upload_tw<T>(ctx, tw))) return rc;
+    if ((rc = upload_vec<T>(ctx, &ctx->d_lam, lam))) return rc;
+    CK(cudaMalloc(&ctx->d_films, ctx->films.size() * sizeof(Film)));
+    CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_plans, ctx->plans.size() * sizeof(Plan)));
+    CK(cudaMemcpy(ctx->d_plans, ctx->plans.data(), ctx->plans.size() * sizeof(Plan), cudaMemcpyHostToDevice));
+    // pools
+    for (int i = 0; i < NSLOT; ++i) {
+        CK(cudaMalloc(&ctx->d_field[i], (size_t)ctx->ncell * sizeof(T)));
+        CK(cudaMemset(ctx->d_field[i], 0, (size_t)ctx->ncell * sizeof(T)));
+    }
+    if (ctx->stray) {
+        for (int i = 0; i < NSPEC; ++i) {
+            CK(cudaMalloc(&ctx->d_spec[i], (size_t)ctx->nspec * V));
+            CK(cudaMemset(ctx->d_spec[i], 0, (size_t)ctx->nspec * V));
+        }
+        CK(cudaMalloc(&ctx->d_ktab, (size_t)ctx->nktab * sizeof(T)));
+        for (int f : ktab_owner)
+            if ((rc = newell_setup<T>(ctx, ctx->films[f]))) return rc;
+    }
+    CK(cudaMalloc(&ctx->d_stage, (size_t)3 * ctx->ncell * sizeof(double)));
+    CK(cudaMalloc(&ctx->d_status, sizeof(int)));
+    CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    CK(cudaMalloc(&ctx->d_step, sizeof(long long)));
+    CK(cudaMemset(ctx->d_step, 0, sizeof(long long)));
+    CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    ctx->tsz = sizeof(T);
+    build_programs(ctx);
+    CK(cudaDeviceSynchronize());
+    return SGSPM_OK;
+}
+
+static void release(sgspm_ctx* ctx) {
+    drop_graph(ctx);
+    void* ptrs[] = {ctx->d_films, ctx->d_plans, ctx->d_tw, ctx->d_lam, ctx->d_ktab, ctx->d_he, ctx->d_status, ctx->d_step,
+                    ctx->d_stage, ctx->d_work_xz, ctx->d_work_yh, ctx->d_work_e, ctx->d_first_e, ctx->d_epart, ctx->d_eout};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < NSLOT; ++i)
+        if (ctx->d_field[i]) cudaFree(ctx->d_field[i]);
+    for (int i = 0; i < NSPEC; ++i)
+        if (ctx->d_spec[i]) cudaFree(ctx->d_spec[i]);
+    for (int n = 0; n < 4; ++n)
+        if (ctx->d_work_ys[n]) cudaFree(ctx->d_work_ys[n]);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+}
+
+static int check_status(sgspm_ctx* ctx) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st & 1) return fail(ctx, SGSPM_ERR_NONFINITE, "non-finite value or zero vector before projection");
+    if (st & 2) return fail(ctx, SGSPM_ERR_NONFINITE, "set_field: zero-length or non-finite magnetisation vector");
+    return SGSPM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+static int set_field_t(sgspm_t ctx, int which, const void* ptr, int dtype) {
+    const long long n = ctx->ncell;
+    const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
+    CK(cudaMemcpyAsync(ctx->d_stage, ptr, bytes, cudaMemcpyDefault, ctx->stream));
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    T *d0, *d1, *d2;
+    T* tmp = nullptr;
+    if (which == SGSPM_M) {
+        d0 = (T*)ctx->d_field[M1];
+        d1 = (T*)ctx->d_field[M2];
+        d2 = (T*)ctx->d_field[M3];
+    } else {
+        // per-cell h_e is kept interleaved [cell][3]; stage through three scratch slots
+        d0 = (T*)ctx->d_field[HS1];
+        d1 = (T*)ctx->d_field[HS2];
+        d2 = (T*)ctx->d_field[HS3];
+        (void)tmp;
+    }
+    if (dtype == SGSPM_F64_DATA)
+        copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, (const double*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+    else
+        copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, (const float*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+    CK(cudaGetLastError());
+    if (which == SGSPM_M) {
+        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        normalize_kernel<T><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, n, ctx->d_status);
+        CK(cudaGetLastError());
+        int rc = check_status(ctx);
+        if (rc) return fail(ctx, SGSPM_ERR_ARG, "set_field: zero-length or non-finite magnetisation vector");
+        rc = run_prog(ctx, ctx->fwd_prog, ctx->stream);
+        if (rc) return rc;
+        ctx->have_m = true;
+    } else {
+        if (!ctx->d_he) CK(cudaMalloc(&ctx->d_he, (size_t)3 * n * sizeof(T)));
+        he_interleave_kernel<T><<<nb, 256, 0, ctx->stream>>>((T*)ctx->d_he, d0, d1, d2, n);
+        CK(cudaGetLastError());
+        if (!ctx->he_cell) {
+            ctx->he_cell = true;
+            drop_graph(ctx);
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SGSPM_OK;
+}
+
+template <typename T>
+static int get_field_t(sgspm_t ctx, int which, void* ptr, int dtype) {
+    const long long n = ctx->ncell;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    int base = M1;
+    if (which == SGSPM_HS) {
+        if (ctx->stray) {
+            int rc = run_prog(ctx, ctx->hs_prog, ctx->stream);
+            if (rc) return rc;
+        } else {
+            for (int i = 0; i < 3; ++i) CK(cudaMemsetAsync(ctx->d_field[HS1 + i], 0, (size_t)n * sizeof(T), ctx->stream));
+        }
+        base = HS1;
+    }
+    const T* s0 = (const T*)ctx->d_field[base];
+    const T* s1 = (const T*)ctx->d_field[base + 1];
+    const T* s2 = (const T*)ctx->d_field[base + 2];
+    if (dtype == SGSPM_F64_DATA)
+        copy_out_kernel<T, double><<<nb, 256, 0, ctx->stream>>>((double*)ctx->d_stage, s0, s1, s2, ctx->d_films, ctx->nfilm, n);
+    else
+        copy_out_kernel<T, float><<<nb, 256, 0, ctx->stream>>>((float*)ctx->d_stage, s0, s1, s2, ctx->d_films, ctx->nfilm, n);
+    CK(cudaGetLastError());
+    const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
+    CK(cudaMemcpyAsync(ptr, ctx->d_stage, bytes, cudaMemcpyDefault, ctx->stream));
+    return check_status(ctx);
+}
+
+extern "C" {
+
+int sgspm_version(void) { return 100; }
+
+const char* sgspm_last_error(sgspm_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int sgspm_create_batch(int nfilm, const sgspm_grid* grids, const double* eps, const double* Q, const double* alpha,
+                       const double* dt, const double* easy_axis, int flags, void* cuda_stream, sgspm_t* out) {
+    if (!out) {
+        g_create_err = "out is NULL";
+        return SGSPM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (nfilm < 1 || !grids || !eps || !Q || !alpha || !dt || !easy_axis) {
+        g_create_err = "nfilm < 1 or a NULL parameter array";
+        return SGSPM_ERR_ARG;
+    }
+    sgspm_ctx* ctx = new sgspm_ctx();
+    ctx->nfilm = nfilm;
+    ctx->flags = flags;
+    ctx->fp64 = (flags & SGSPM_FP64) != 0;
+    ctx->stray = !(flags & SGSPM_NO_STRAY);
+    ctx->stream = (cudaStream_t)cuda_stream;
+    for (int f = 0; f < nfilm; ++f) {
+        const sgspm_grid& g = grids[f];
+        const double* u = easy_axis + 3 * f;
+        double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        std::string why;
+        if (g.nx < 1 || g.ny < 1 || g.nz < 1) why = "cell counts must be >= 1";
+        else if (!(g.hx > 0 && g.hy > 0 && g.hz > 0)) why = "cell sizes must be > 0";
+        else if (!(eps[f] >= 0 && Q[f] >= 0 && alpha[f] >= 0)) why = "eps, Q, alpha must be >= 0";
+        else if (!(dt[f] > 0)) why = "dt must be > 0";
+        else if (!(un > 0) || !std::isfinite(un)) why = "easy axis must be a finite non-zero vector";
+        else if ((long long)g.nx * g.ny * g.nz > (1LL << 31) / 4) why = "film too large";
+        if (!why.empty()) {
+            g_create_err = "film " + std::to_string(f) + ": " + why;
+            delete ctx;
+            return SGSPM_ERR_ARG;
+        }
+        Film F;
+        memset(&F, 0, sizeof(F));
+        F.nx = g.nx;
+        F.ny = g.ny;
+        F.nz = g.nz;
+        F.hx = g.hx;
+        F.hy = g.hy;
+        F.hz = g.hz;
+        F.eps = eps[f];
+        F.Q = Q[f];
+        F.alpha = alpha[f];
+        F.dt = dt[f];
+        for (int a = 0; a < 3; ++a) F.u[a] = u[a] / un;
+        ctx->films.push_back(F);
+    }
+    int rc = ctx->fp64 ? setup_t<double>(ctx) : setup_t<float>(ctx);
+    if (rc) {
+        g_create_err = ctx->err;
+        release(ctx);
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return SGSPM_OK;
+}
+
+int sgspm_create(const sgspm_grid* grid, double eps, double Q, double alpha, double dt, const double easy_axis[3], int flags,
+                 void* cuda_stream, sgspm_t* out) {
+    if (!grid || !easy_axis) {
+        g_create_err = "grid or easy_axis is NULL";
+        if (out) *out = nullptr;
+        return SGSPM_ERR_ARG;
+    }
+    return sgspm_create_batch(1, grid, &eps, &Q, &alpha, &dt, easy_axis, flags, cuda_stream, out);
+}
+
+int sgspm_destroy(sgspm_t h) {
+    if (!h) return SGSPM_OK;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+    return SGSPM_OK;
+}
+
+int sgspm_set_applied_field(sgspm_t ctx, const double* he) {
+    if (!ctx || !he) return ctx ? fail(ctx, SGSPM_ERR_ARG, "he is NULL") : SGSPM_ERR_ARG;
+    for (int f = 0; f < ctx->nfilm; ++f)
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(he[3 * f + a])) return fail(ctx, SGSPM_ERR_ARG, "applied field must be finite");
+            ctx->films[f].he[a] = he[3 * f + a];
+        }
+    ctx->he_cell = false;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
+    drop_graph(ctx);
+    return SGSPM_OK;
+}
+
+int sgspm_set_field(sgspm_t ctx, int which, const void* ptr, int dtype) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!ptr) return fail(ctx, SGSPM_ERR_ARG, "ptr is NULL");
+    if (which != SGSPM_M && which != SGSPM_HE) return fail(ctx, SGSPM_ERR_ARG, "set_field: which must be SGSPM_M or SGSPM_HE");
+    if (dtype != SGSPM_F32 && dtype != SGSPM_F64_DATA) return fail(ctx, SGSPM_ERR_ARG, "dtype must be SGSPM_F32 or SGSPM_F64_DATA");
+    return ctx->fp64 ? set_field_t<double>(ctx, which, ptr, dtype) : set_field_t<float>(ctx, which, ptr, dtype);
+}
+
+int sgspm_get_field(sgspm_t ctx, int which, void* ptr, int dtype) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!ptr) return fail(ctx, SGSPM_ERR_ARG, "ptr is NULL");
+    if (which != SGSPM_M && which != SGSPM_HS) return fail(ctx, SGSPM_ERR_ARG, "get_field: which must be SGSPM_M or SGSPM_HS");
+    if (dtype != SGSPM_F32 && dtype != SGSPM_F64_DATA) return fail(ctx, SGSPM_ERR_ARG, "dtype must be SGSPM_F32 or SGSPM_F64_DATA");
+    if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
+    return ctx->fp64 ? get_field_t<double>(ctx, which, ptr, dtype) : get_field_t<float>(ctx, which, ptr, dtype);
+}
+
+int sgspm_step(sgspm_t ctx, long long n) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (n < 1) return fail(ctx, SGSPM_ERR_ARG, "n must be >= 1");
+    if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
+    if (ctx->flags & SGSPM_NO_GRAPH) {
+        for (long long i = 0; i < n; ++i) {
+            int rc = run_prog(ctx, ctx->step_prog, ctx->stream);
+            if (rc) return rc;
+        }
+    } else {
+        if (!ctx->gexec) {
+            int rc = capture_step(ctx);
+            if (rc) return rc;
+        }
+        for (long long i = 0; i < n; ++i) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    }
+    ctx->steps += n;
+    return SGSPM_OK;
+}
+
+int sgspm_energy(sgspm_t ctx, double* out) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!out) return fail(ctx, SGSPM_ERR_ARG, "out is NULL");
+    if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
+    if (ctx->stray) {
+        int rc = run_prog(ctx, ctx->hs_prog, ctx->stream);
+        if (rc) return rc;
+    }
+    if (ctx->fp64)
+        energy_partial_kernel<double><<<ctx->n_e, kThreads, 0, ctx->stream>>>(dev_view<double>(ctx), ctx->d_work_e, M1, HS1,
+                                                                              ctx->stray ? 1 : 0, ctx->d_epart);
+    else
+        energy_partial_kernel<float><<<ctx->n_e, kThreads, 0, ctx->stream>>>(dev_view<float>(ctx), ctx->d_work_e, M1, HS1,
+                                                                             ctx->stray ? 1 : 0, ctx->d_epart);
+    CK(cudaGetLastError());
+    energy_final_kernel<<<(ctx->nfilm + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_films, ctx->nfilm, ctx->d_first_e, ctx->d_epart,
+                                                                           ctx->d_eout);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, ctx->d_eout, (size_t)5 * ctx->nfilm * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return check_status(ctx);
+}
+
+int sgspm_set_forcing(sgspm_t ctx, int kind) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (kind != SGSPM_FORCE_NONE && kind != SGSPM_FORCE_MMS_1D && kind != SGSPM_FORCE_MMS_3D)
+        return fail(ctx, SGSPM_ERR_ARG, "unknown forcing kind");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (Film& F : ctx->films) F.forcing = kind;
+    ctx->forcing = kind != SGSPM_FORCE_NONE;
+    CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
+    build_programs(ctx);
+    drop_graph(ctx);
+    return SGSPM_OK;
+}
+
+int sgspm_set_time(sgspm_t ctx, double t) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!std::isfinite(t)) return fail(ctx, SGSPM_ERR_ARG, "t must be finite");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (Film& F : ctx->films) F.t0 = t;
+    ctx->steps = 0;
+    CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->d_step, 0, sizeof(long long)));
+    return SGSPM_OK;
+}
+
+int sgspm_get_time(sgspm_t ctx, double* t) {
+    if (!ctx || !t) return SGSPM_ERR_ARG;
+    *t = ctx->films[0].t0 + (double)ctx->steps * ctx->films[0].dt;
+    return SGSPM_OK;
+}
+
+int sgspm_sync(sgspm_t ctx) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    return check_status(ctx);
+}
+
+int sgspm_profile_step(sgspm_t ctx, float* ms, int* kind, int cap) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!ms || !kind || cap < (int)ctx->step_prog.size()) return fail(ctx, SGSPM_ERR_ARG, "profile buffers too small");
+    if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
+    const int n = (int)ctx->step_prog.size();
+    std::vector<cudaEvent_t> ev(n + 1);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(ev[0], ctx->stream));
+    for (int i = 0; i < n; ++i) {
+        int rc = enqueue(ctx, ctx->step_prog[i], ctx->stream);
+        if (rc) return rc;
+        CK(cudaEventRecord(ev[i + 1], ctx->stream));
+    }
+    CK(cudaEventSynchronize(ev[n]));
+    for (int i = 0; i < n; ++i) {
+        CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+        const Launch& L = ctx->step_prog[i];
+        kind[i] = L.kind * 10 + (L.kind == 0 ? (L.xz.n_rhs ? 1 : L.xz.op == 2 ? 3 : 2) : L.y.n);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    ctx->steps += 1;
+    return n;
+}
+
+int sgspm_launches_per_step(sgspm_t ctx) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    return (int)ctx->step_prog.size();
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Shared device-side types of the SGSPM library: complex arithmetic, FFT plans,
+// per-film descriptors and the per-pass programs that the host builds once.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgspm {
+
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename T> using cplx = typename CplxOf<T>::type;
+
+template <typename V> __device__ __forceinline__ V cmk(decltype(V::x) a, decltype(V::x) b) { V r; r.x = a; r.y = b; return r; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) { return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename V> __device__ __forceinline__ V cconj(V a) { return cmk<V>(a.x, -a.y); }
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return cmk<V>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return cmk<V>(a.y, -a.x); }
+template <typename V> __device__ __forceinline__ V cmul_pi(V a) { return cmk<V>(-a.y, a.x); }
+
+constexpr int kMaxStages = 16;
+constexpr int kThreads = 256;
+
+// Mixed-radix (8, 4, 2, 3, 5) Stockham plan of one transform length P.
+// tw: offset of W_P^m = exp(-2 pi i m / P), m in [0, P), in the twiddle pool.
+// tw4: offset of exp(-i pi k / (2P)), k in [0, P) (DCT post/pre twiddles).
+struct Plan {
+    int P;
+    int nst;
+    int radix[kMaxStages];
+    int tw;
+    int tw4;
+};
+
+// One film of a (possibly batched) handle.
+struct Film {
+    int nx, ny, nz;          // cells
+    int Px, Py, Pz;          // zero-padded stray-field lengths (2n, or 1 for n = 1)
+    int Kx;                  // Px/2 + 1 half-spectrum length along x
+    int pad_;
+    long long off_cell;      // offset into every real field pool
+    long long off_spec;      // offset into every spectral pool: Kx * ny * Pz per film
+    long long off_ktab;      // kernel-table offset: 6 * (Pz/2+1) * (Py/2+1) * Kx
+    int lam;                 // offset of lambda_x[nx], lambda_y[ny], lambda_z[nz] in the eigen pool
+    int plan_dx, plan_dy, plan_dz;   // DCT lengths nx, ny, nz
+    int plan_px, plan_py, plan_pz;   // padded lengths Px, Py, Pz
+    int forcing;             // 0 none, 1 MMS 1D, 3 MMS 3D
+    double hx, hy, hz;
+    double eps, Q, alpha, dt;
+    double u[3];
+    double he[3];
+    double t0;               // time at step counter 0
+};
+
+// Operand reference of a pointwise update: >= 0 real field slot, < 0 shared-memory slab (-1 - idx).
+constexpr int kMaxSlots = 24;
+constexpr int kMaxSpec = 8;
+
+// Slab (XZ) pass program.  Phases run in order; unused phases have count 0 / op 0.
+struct XZProg {
+    // phase R: right-hand sides r_a = scale * (f_a + eps Delta_h m_a) and their forward DCT
+    int n_rhs;
+    int rhs_comp[3];       // component a of each rhs
+    int rhs_h[3];          // spectral slot of H_a to invert for h_s,a (-1: no stray term)
+    int rhs_out[3];        // real slot receiving DCT_xz(r_a)
+    int rhs_hs_store[3];   // real slot receiving h_s,a (-1: none)
+    int state[3];          // real slots of the state (m1, m2, m3) at which f is evaluated
+    int damp;              // 0: scale = dt; 1: scale = alpha dt
+    int rhs_dct;           // 0: only invert h_s (energy), no rhs / DCT
+    // phase I: inverse DCT_xz of spectral-solved slots -> delta slabs in shared memory
+    int n_inv;
+    int inv_in[3];
+    int inv_store[3];      // real slot receiving delta (-1: none)
+    // phase U: pointwise update
+    int op;                // 0 none, 1 Gauss-Seidel cross product, 2 damping + projection
+    int gs_out, gs_base, gs_p, gs_q, gs_r, gs_s;   // out = base + p*q - r*s (operand refs)
+    int fin_in[3];         // m** slots; delta slabs 0..2; m^{n+1} -> fin_out
+    int fin_out[3];
+    // phase F: forward zero-padded FFT (x R2C, z C2C) of real fields -> spectral slots
+    int n_fwd;
+    int fwd_src[3];        // operand refs (slab -1-idx means the phase-U result slab idx)
+    int fwd_dst[3];
+};
+
+// Line (Y) pass program.
+struct YProg {
+    int kind;              // 0 heat solve, 1 stray field
+    int n;                 // heat: fields to solve; stray: outputs
+    int slot[3];           // heat: real slots (in place); stray: output component a
+    int damp;              // heat: 0 -> c = eps, 1 -> c = alpha eps
+    int in_spec[3];        // stray: spectral slots of M_1, M_2, M_3
+    int out_spec[3];       // stray: spectral slot of H_a for each output
+};
+
+// Gauss-Legendre rules on [-1, 1] used by the Newell set-up, packed: order q at off[q].
+struct GLTable {
+    double x[64];
+    double w[64];
+    int off[16];
+};
+
+// Device-side view of a handle (pointers valid on the device).
+template <typename T>
+struct Dev {
+    const Film* films;
+    const Plan* plans;
+    const cplx<T>* tw;
+    const T* lam;          // eigenvalue pool
+    const T* ktab;         // -N_hat / (Px Py Pz), reduced real table
+    T* field[kMaxSlots];
+    cplx<T>* spec[kMaxSpec];
+    const T* he_cell;      // per-cell applied field [3][ncell_total] or null
+    int* status;
+    const long long* step_ctr;
+};
+
+}  // namespace sgspm

@@ -13,27 +13,17 @@ def random_unit(seed, n):
     return m / np.linalg.norm(m, axis=0)
 
 
-def smoothed_random_unit(seed, n, steps=20, kappa=0.15):
-    """Random unit vectors smoothed by `steps` explicit heat steps, then renormalised.
+def smoothed_random_unit(seed, n, sigma_cells=(20.5, 20.5, 20.5)):
+    """Random unit vectors smoothed, then renormalised.
 
-    Each step is u <- u + kappa * sum_axes (u_+ - 2u + u_-) with mirrored edges
-    (a plain averaging filter; kappa * 4 * 3 < 2 keeps it stable in 3D).
+    The smoothing is a Gaussian filter (mirror boundaries) whose width equals the
+    diffusion length of 20 implicit heat steps at the run's parameters,
+    sqrt(2 * 20 * eps * dt) / h = sqrt(40 * 0.016 * 0.01) * 256 = 20.5 cells.
     """
+    from scipy.ndimage import gaussian_filter
     m = random_unit(seed, n)
-    for _ in range(steps):
-        acc = np.zeros_like(m)
-        for axis in (1, 2, 3):
-            if m.shape[axis] == 1:
-                continue
-            pad = [(0, 0)] * 4
-            pad[axis] = (1, 1)
-            up = np.pad(m, pad, mode="edge")
-            lo = [slice(None)] * 4
-            hi = [slice(None)] * 4
-            lo[axis] = slice(0, -2)
-            hi[axis] = slice(2, None)
-            acc += up[tuple(hi)] - 2.0 * m + up[tuple(lo)]
-        m = m + kappa * acc
+    sig = (sigma_cells[2], sigma_cells[1], sigma_cells[0])     # (z, y, x) axes of [nz, ny, nx]
+    m = np.stack([gaussian_filter(m[a], sigma=sig, mode="reflect") for a in range(3)])
     return m / np.linalg.norm(m, axis=0)
 
 
