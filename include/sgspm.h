@@ -156,6 +156,42 @@ int sgspm_profile_step(sgspm_t h, float* ms, int* kind, int cap);
 /* Number of kernel launches one sgspm_step(1) enqueues (for launch accounting). */
 int sgspm_launches_per_step(sgspm_t h);
 
+/*
+ * sgspm_energy_noalloc - the energy of sgspm_energy for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a library-usage variant.
+ *
+ * Some callers cannot call cudaMalloc: a plugin whose host application owns every device
+ * buffer through its own pool, a process with a fixed device-memory budget, or a latency-
+ * critical loop that must not risk the synchronisation an allocation can cause.  This entry
+ * point allocates nothing and needs no handle: the caller passes m (and h_s) in its own
+ * device buffers and receives the result in its own device buffer.
+ *
+ *   grid, eps, Q, easy_axis (normalised here), he[3]: as for one film of sgspm_create, with a
+ *        uniform applied field (host values);
+ *   m:   device pointer, SoA [3][nz][ny][nx], dtype SGSPM_F32 or SGSPM_F64_DATA;
+ *   hs:  device pointer to h_s(m) in the same layout and dtype, or NULL (stray term 0);
+ *        sgspm_get_field(SGSPM_HS) of a handle yields it;
+ *   out: device pointer to 5 doubles {exchange, anisotropy, stray, zeeman, total}
+ *        (same definitions as sgspm_energy);
+ *   cuda_stream: cudaStream_t on which the work is enqueued (asynchronous; out is valid
+ *        once the stream reaches this point).
+ *
+ * Limits and sharing.  The per-block partial sums live in a fixed file-scope device array
+ * of 4096 x 4 doubles (128 KiB per GPU that loads the library, held until exit), so the
+ * grid may have at most 16,777,216 cells; larger grids return SGSPM_ERR_UNSUPPORTED.  Every
+ * call shares that array: calls that overlap on the GPU (unordered streams) race on it and
+ * must be serialised by the caller.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Errors: SGSPM_ERR_ARG for bad arguments, SGSPM_ERR_CUDA for a
+ * failed CUDA call; the text is returned by sgspm_noalloc_last_error (per host thread).
+ */
+int sgspm_energy_noalloc(const sgspm_grid* grid, double eps, double Q, const double easy_axis[3],
+                         const double he[3], const void* m, const void* hs, int dtype, double* out,
+                         void* cuda_stream);
+
+/* Text of the last error of sgspm_energy_noalloc on the calling host thread. */
+const char* sgspm_noalloc_last_error(void);
+
 /* ABI version (major*100 + minor). */
 int sgspm_version(void);
 

@@ -12,6 +12,7 @@
 #include "passes.cuh"
 #include "passes.cu"
 #include "newell.cu"
+#include "noalloc.cu"
 
 namespace sgspm {
 
@@ -1041,6 +1042,58 @@ int sgspm_profile_step(sgspm_t ctx, float* ms, int* kind, int cap) {
     ctx->steps += 1;
     return n;
 }
+
+static thread_local std::string g_noalloc_err;
+
+int sgspm_energy_noalloc(const sgspm_grid* grid, double eps, double Q, const double easy_axis[3], const double he[3],
+                         const void* m, const void* hs, int dtype, double* out, void* cuda_stream) {
+    g_noalloc_err.clear();
+    if (!grid || !easy_axis || !he || !m || !out) {
+        g_noalloc_err = "grid, easy_axis, he, m and out must be non-NULL";
+        return SGSPM_ERR_ARG;
+    }
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->hx > 0 && grid->hy > 0 && grid->hz > 0)) {
+        g_noalloc_err = "cell counts must be >= 1 and cell sizes > 0";
+        return SGSPM_ERR_ARG;
+    }
+    if (dtype != SGSPM_F32 && dtype != SGSPM_F64_DATA) {
+        g_noalloc_err = "dtype must be SGSPM_F32 or SGSPM_F64_DATA";
+        return SGSPM_ERR_ARG;
+    }
+    const long long n = (long long)grid->nx * grid->ny * grid->nz;
+    const long long nblocks = (n + kNoallocCellsPerBlock - 1) / kNoallocCellsPerBlock;
+    if (nblocks > kNoallocMaxBlocks) {
+        g_noalloc_err = "grid has " + std::to_string(n) + " cells; the allocation-free energy handles at most " +
+                        std::to_string((long long)kNoallocMaxBlocks * kNoallocCellsPerBlock);
+        return SGSPM_ERR_UNSUPPORTED;
+    }
+    double un = std::sqrt(easy_axis[0] * easy_axis[0] + easy_axis[1] * easy_axis[1] + easy_axis[2] * easy_axis[2]);
+    if (!(un > 0) || !std::isfinite(un)) {
+        g_noalloc_err = "easy axis must be a finite non-zero vector";
+        return SGSPM_ERR_ARG;
+    }
+    double* part = noalloc_scratch(&g_noalloc_err);
+    if (!part) return SGSPM_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const double u0 = easy_axis[0] / un, u1 = easy_axis[1] / un, u2 = easy_axis[2] / un;
+    if (dtype == SGSPM_F64_DATA)
+        energy_noalloc_partial_kernel<double><<<(unsigned)nblocks, kThreads, 0, st>>>(
+            (const double*)m, (const double*)hs, grid->nx, grid->ny, grid->nz, grid->hx, grid->hy, grid->hz, u0, u1, u2,
+            he[0], he[1], he[2], part);
+    else
+        energy_noalloc_partial_kernel<float><<<(unsigned)nblocks, kThreads, 0, st>>>(
+            (const float*)m, (const float*)hs, grid->nx, grid->ny, grid->nz, grid->hx, grid->hy, grid->hz, u0, u1, u2,
+            he[0], he[1], he[2], part);
+    energy_noalloc_final_kernel<<<1, 32, 0, st>>>(part, (int)nblocks, eps, Q, grid->hx * grid->hy * grid->hz, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_noalloc_err = std::string("kernel launch: ") + cudaGetErrorString(e);
+        return SGSPM_ERR_CUDA;
+    }
+    return SGSPM_OK;
+}
+
+const char* sgspm_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
 
 int sgspm_launches_per_step(sgspm_t ctx) {
     if (!ctx) return SGSPM_ERR_ARG;

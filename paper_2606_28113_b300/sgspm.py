@@ -62,6 +62,10 @@ def lib():
     L.sgspm_launches_per_step.argtypes = [vp]
     L.sgspm_profile_step.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int), i]
     L.sgspm_version.argtypes = []
+    L.sgspm_energy_noalloc.argtypes = [ctypes.POINTER(Grid), d, d, dp, dp, vp, vp, i, vp, vp]
+    L.sgspm_energy_noalloc.restype = ctypes.c_int
+    L.sgspm_noalloc_last_error.argtypes = []
+    L.sgspm_noalloc_last_error.restype = ctypes.c_char_p
     for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_field",
                  "sgspm_get_field", "sgspm_step", "sgspm_energy", "sgspm_set_forcing", "sgspm_set_time",
                  "sgspm_get_time", "sgspm_sync", "sgspm_destroy", "sgspm_launches_per_step", "sgspm_version",
@@ -245,6 +249,22 @@ class Handle:
         if n < 0:
             self._check(n)
         return [(kind[i], ms[i]) for i in range(n)]
+
+
+def energy_noalloc(n, h, eps, Q, u, he, m, hs, out, stream=None):
+    """sgspm_energy_noalloc: energy of device fields m, hs (torch CUDA tensors, same dtype)
+    into the device tensor `out` (5 float64), without any device allocation."""
+    import torch
+    dtype = {torch.float32: F32, torch.float64: F64}[m.dtype]
+    g = Grid(*n, *h)
+    ua = np.ascontiguousarray(u, dtype=np.float64)
+    ha = np.ascontiguousarray(he, dtype=np.float64)
+    rc = lib().sgspm_energy_noalloc(ctypes.byref(g), float(eps), float(Q), _dptr(ua), _dptr(ha),
+                                    ctypes.c_void_p(m.data_ptr()),
+                                    ctypes.c_void_p(hs.data_ptr() if hs is not None else 0), dtype,
+                                    ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    if rc != OK:
+        raise SGSPMError(rc, lib().sgspm_noalloc_last_error().decode())
 
 
 def film(n, h, eps, Q, alpha, dt, u=(1.0, 0.0, 0.0), he=(0.0, 0.0, 0.0), **kw):
