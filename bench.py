@@ -148,13 +148,20 @@ def run_reference(args):
 
 
 # algorithmic bytes per cell of each launch kind, FP32 (field crossings x 4 B; see the design notes)
-def algorithmic_bytes_per_cell(kind):
+def algorithmic_bytes_per_cell(kind, ncomp=1):
     k, v = divmod(kind, 10)
     if k == 2:            # stray refresh operator: changed inputs read + outputs written
         reads = 3 if v == 2 else 1
         return 4 * (reads + v)
     if k == 1:            # heat solve: read rhs, write solution, per field
         return 4 * 2 * v
+    if k == 0:
+        if v == 1:        # right-hand sides: read m_a and h_s,a, write r_a, per component
+            return 4 * 3 * ncomp
+        if v == 2:        # Gauss-Seidel update: read delta, base, two operands, stored delta; write m
+            return 4 * 6
+        if v == 3:        # damping update + projection: read m** (3) and delta (3), write m (3)
+            return 4 * 9
     return None
 
 
@@ -218,7 +225,11 @@ def run_gpu(args):
     # roofline of the dominant launch variant of the dominant kernel
     dom_kind = max((k for k in share if k // 10 == dom_type), key=lambda k: share[k])
     dom_ms = float(np.mean(prof[dom_kind]))
-    bpc = algorithmic_bytes_per_cell(dom_kind)
+    # the right-hand-side slab pass handles 2 components (start of step) or 1 or 3; weight by launches
+    ncomp = 1.0
+    if dom_kind == 1:
+        ncomp = 8.0 / 6.0     # per step: {2, 1, 1, 1, 1, 3} components over 6 launches (SGSPM, R1)
+    bpc = algorithmic_bytes_per_cell(dom_kind, ncomp)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     roof = None

@@ -48,8 +48,10 @@ struct sgspm_ctx {
     Plan* d_plans = nullptr;
     void* d_tw = nullptr;
     void* d_lam = nullptr;
+    void* d_dtab = nullptr;
     void* d_ktab = nullptr;
     void* d_field[NSLOT] = {};
+    void* d_flo[NSLOT] = {};           // low parts of the double-float state slots (FP32 form)
     void* d_spec[NSPEC] = {};
     void* d_he = nullptr;
     bool he_cell = false;
@@ -65,12 +67,17 @@ struct sgspm_ctx {
     int n_ys[4] = {};
     int tx_s[4] = {};
     size_t smem_xz = 0, smem_yh = 0, smem_ys[4] = {};
+    bool warp_stray = false;           // register-resident stray line pass (all Py in 64..512)
+    int4* d_work_yw = nullptr;
+    int n_yw = 0;
+    size_t smem_yw = 0;
     int4* d_work_e = nullptr;
     int n_e = 0;
     int* d_first_e = nullptr;
     double* d_epart = nullptr;
     double* d_eout = nullptr;
     std::vector<Launch> step_prog, hs_prog, fwd_prog;
+    std::vector<double> dtab_host;     // dense short-axis DCT tables, built with the plans
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool have_m = false;
@@ -147,8 +154,10 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
     d.plans = ctx->d_plans;
     d.tw = (const cplx<T>*)ctx->d_tw;
     d.lam = (const T*)ctx->d_lam;
+    d.dtab = (const T*)ctx->d_dtab;
     d.ktab = (const T*)ctx->d_ktab;
     for (int i = 0; i < kMaxSlots; ++i) d.field[i] = i < NSLOT ? (T*)ctx->d_field[i] : nullptr;
+    for (int i = 0; i < kMaxSlots; ++i) d.flo[i] = i < NSLOT ? (T*)ctx->d_flo[i] : nullptr;
     for (int i = 0; i < kMaxSpec; ++i) d.spec[i] = i < NSPEC ? (cplx<T>*)ctx->d_spec[i] : nullptr;
     d.he_cell = ctx->he_cell ? (const T*)ctx->d_he : nullptr;
     d.status = ctx->d_status;
@@ -168,7 +177,14 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
             break;
         case 2: {
             int n = L.y.n;
-            y_stray_kernel<T><<<ctx->n_ys[n], kThreads, ctx->smem_ys[n], st>>>(d, ctx->d_work_ys[n], L.y, ctx->tx_s[n]);
+            if (ctx->warp_stray) {
+                const unsigned nb = (unsigned)ctx->n_yw, nt = 32 * kWarpLines;
+                if (n == 1) y_stray_warp_kernel<T, 1><<<nb, nt, ctx->smem_yw, st>>>(d, ctx->d_work_yw, L.y);
+                else if (n == 2) y_stray_warp_kernel<T, 2><<<nb, nt, ctx->smem_yw, st>>>(d, ctx->d_work_yw, L.y);
+                else y_stray_warp_kernel<T, 3><<<nb, nt, ctx->smem_yw, st>>>(d, ctx->d_work_yw, L.y);
+            } else {
+                y_stray_kernel<T><<<ctx->n_ys[n], kThreads, ctx->smem_ys[n], st>>>(d, ctx->d_work_ys[n], L.y, ctx->tx_s[n]);
+            }
             break;
         }
         default:
@@ -470,6 +486,23 @@ static int get_plan(sgspm_ctx* ctx, int P, std::vector<double2>& tw) {
         cis(k, 4LL * P, &c, &s);
         tw.push_back(make_double2(c, -s));
     }
+    pl.dtab = -1;
+    if (P <= 16) {
+        // C[k][n] = cos(pi k (2n+1) / (2P));  Ci[n][k] = (k ? 2 : 1) C[k][n]
+        pl.dtab = (int)ctx->dtab_host.size();
+        for (int k = 0; k < P; ++k)
+            for (int n = 0; n < P; ++n) {
+                double c, s;
+                cis((long long)k * (2 * n + 1), 4LL * P, &c, &s);
+                ctx->dtab_host.push_back(c);
+            }
+        for (int n = 0; n < P; ++n)
+            for (int k = 0; k < P; ++k) {
+                double c, s;
+                cis((long long)k * (2 * n + 1), 4LL * P, &c, &s);
+                ctx->dtab_host.push_back(k ? 2.0 * c : c);
+            }
+    }
     int id = (int)ctx->plans.size();
     ctx->plans.push_back(pl);
     ctx->plan_of[P] = id;
@@ -553,7 +586,7 @@ static int newell_setup(sgspm_ctx* ctx, const Film& F) {
         newell_axis_kernel<<<(unsigned)((nC + 255) / 256), 256>>>(B, C, 2, nz, Hz, F.Pz, Hy * Kx, 1, (long long)Hy * Kx, 1, 0,
                                                                  (long long)nz * Hy * Kx, (long long)Hy * Kx, 1, 0,
                                                                  (long long)Hz * Hy * Kx, cs(2), sn(2));
-        newell_finish_kernel<T><<<(unsigned)((nC + 255) / 256), 256>>>(C, (T*)ctx->d_ktab + F.off_ktab, nC / 6,
+        newell_finish_kernel<T><<<(unsigned)((nC + 255) / 256), 256>>>(C, (T*)ctx->d_ktab + F.off_ktab, Kx, Hy, Hz,
                                                                        1.0 / ((double)F.Px * F.Py * F.Pz));
         e = cudaGetLastError();
     }
@@ -572,6 +605,7 @@ static int setup_t(sgspm_ctx* ctx) {
     const size_t V = sizeof(cplx<T>);
     std::vector<double2> tw;
     std::vector<double> lam;
+    ctx->dtab_host.clear();
     // plans, offsets
     long long oc = 0, os = 0, ok = 0;
     std::map<std::vector<double>, long long> ktab_of;
@@ -637,18 +671,18 @@ static int setup_t(sgspm_ctx* ctx) {
         if (F.ny > maxny) maxny = F.ny;
     }
     ctx->tx_h = 8;
-    sy = (size_t)2 * ((ctx->tx_h + 1) / 2) * maxny * V + (size_t)ctx->tx_h * maxny * sizeof(T);
+    sy = (size_t)2 * maxny * V + (size_t)2 * ((ctx->tx_h + 1) / 2) * maxny * V + (size_t)ctx->tx_h * (maxny + 8) * sizeof(T);
     if (sx > (size_t)smem_max || sy > (size_t)smem_max)
         return fail(ctx, SGSPM_ERR_UNSUPPORTED, "slab of " + std::to_string(sx) + " B does not fit in shared memory");
     ctx->smem_xz = sx;
     ctx->smem_yh = sy;
     for (int n = 1; n <= 3; ++n) {
         const size_t budget = 100 * 1024;
-        int tx = (int)(budget / ((2 + n) * (size_t)maxPy * V));
+        int tx = (int)(budget / ((2 + n) * (size_t)(maxPy + 4) * V));
         if (tx > 16) tx = 16;
         if (tx < 1) tx = 1;
         ctx->tx_s[n] = tx;
-        ctx->smem_ys[n] = (size_t)(2 + n) * tx * maxPy * V;
+        ctx->smem_ys[n] = (size_t)maxPy * V + (size_t)(2 + n) * tx * (maxPy + 4) * V;
         if (ctx->smem_ys[n] > (size_t)smem_max)
             return fail(ctx, SGSPM_ERR_UNSUPPORTED, "y line of length " + std::to_string(maxPy) + " does not fit in shared memory");
     }
@@ -691,6 +725,24 @@ static int setup_t(sgspm_ctx* ctx) {
         if ((rc = up4(&ctx->d_work_ys[n], ws))) return rc;
         ctx->n_ys[n] = (int)ws.size();
     }
+    // register-resident stray pass when every film's padded y length is 64..512
+    ctx->warp_stray = ctx->stray;
+    for (const Film& F : ctx->films)
+        if (!(F.Py == 64 || F.Py == 128 || F.Py == 256 || F.Py == 512)) ctx->warp_stray = false;
+    if (ctx->warp_stray) {
+        std::vector<int4> ws;
+        for (int f = 0; f < ctx->nfilm; ++f) {
+            const Film& F = ctx->films[f];
+            for (int kz = 0; kz < F.Pz; ++kz)
+                for (int x0 = 0; x0 < F.Kx; x0 += kWarpLines) ws.push_back(make_int4(f, kz, x0, std::min(kWarpLines, F.Kx - x0)));
+        }
+        if ((rc = up4(&ctx->d_work_yw, ws))) return rc;
+        ctx->n_yw = (int)ws.size();
+        ctx->smem_yw = (size_t)(1 + kWarpLines) * maxPy * V;
+        CK(cudaFuncSetAttribute(y_stray_warp_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yw));
+        CK(cudaFuncSetAttribute(y_stray_warp_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yw));
+        CK(cudaFuncSetAttribute(y_stray_warp_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yw));
+    }
     CK(cudaMalloc(&ctx->d_first_e, first_e.size() * sizeof(int)));
     CK(cudaMemcpy(ctx->d_first_e, first_e.data(), first_e.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_epart, std::max(1, ctx->n_e) * 4 * sizeof(double)));
@@ -698,6 +750,8 @@ static int setup_t(sgspm_ctx* ctx) {
     // tables
     if ((rc = upload_tw<T>(ctx, tw))) return rc;
     if ((rc = upload_vec<T>(ctx, &ctx->d_lam, lam))) return rc;
+    if (ctx->dtab_host.empty()) ctx->dtab_host.push_back(0.0);
+    if ((rc = upload_vec<T>(ctx, &ctx->d_dtab, ctx->dtab_host))) return rc;
     CK(cudaMalloc(&ctx->d_films, ctx->films.size() * sizeof(Film)));
     CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_plans, ctx->plans.size() * sizeof(Plan)));
@@ -706,6 +760,14 @@ static int setup_t(sgspm_ctx* ctx) {
     for (int i = 0; i < NSLOT; ++i) {
         CK(cudaMalloc(&ctx->d_field[i], (size_t)ctx->ncell * sizeof(T)));
         CK(cudaMemset(ctx->d_field[i], 0, (size_t)ctx->ncell * sizeof(T)));
+    }
+    if (sizeof(T) == 4) {
+        // FP32 form: the magnetisation states are double-float (hi + lo) so that rounding of the
+        // O(1) state does not accumulate over many steps; transforms use the hi part only
+        for (int i = M1; i <= B2; ++i) {
+            CK(cudaMalloc(&ctx->d_flo[i], (size_t)ctx->ncell * sizeof(T)));
+            CK(cudaMemset(ctx->d_flo[i], 0, (size_t)ctx->ncell * sizeof(T)));
+        }
     }
     if (ctx->stray) {
         for (int i = 0; i < NSPEC; ++i) {
@@ -730,12 +792,15 @@ static int setup_t(sgspm_ctx* ctx) {
 
 static void release(sgspm_ctx* ctx) {
     drop_graph(ctx);
-    void* ptrs[] = {ctx->d_films, ctx->d_plans, ctx->d_tw, ctx->d_lam, ctx->d_ktab, ctx->d_he, ctx->d_status, ctx->d_step,
-                    ctx->d_stage, ctx->d_work_xz, ctx->d_work_yh, ctx->d_work_e, ctx->d_first_e, ctx->d_epart, ctx->d_eout};
+    void* ptrs[] = {ctx->d_films, ctx->d_plans, ctx->d_tw, ctx->d_lam, ctx->d_dtab, ctx->d_ktab, ctx->d_he, ctx->d_status, ctx->d_step,
+                    ctx->d_stage, ctx->d_work_xz, ctx->d_work_yh, ctx->d_work_e, ctx->d_first_e, ctx->d_epart, ctx->d_eout,
+                    ctx->d_work_yw};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    for (int i = 0; i < NSLOT; ++i)
+    for (int i = 0; i < NSLOT; ++i) {
         if (ctx->d_field[i]) cudaFree(ctx->d_field[i]);
+        if (ctx->d_flo[i]) cudaFree(ctx->d_flo[i]);
+    }
     for (int i = 0; i < NSPEC; ++i)
         if (ctx->d_spec[i]) cudaFree(ctx->d_spec[i]);
     for (int n = 0; n < 4; ++n)
@@ -761,27 +826,30 @@ static int set_field_t(sgspm_t ctx, int which, const void* ptr, int dtype) {
     const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
     CK(cudaMemcpyAsync(ctx->d_stage, ptr, bytes, cudaMemcpyDefault, ctx->stream));
     const unsigned nb = (unsigned)((n + 255) / 256);
-    T *d0, *d1, *d2;
-    T* tmp = nullptr;
+    T *d0, *d1, *d2, *l0 = nullptr, *l1 = nullptr, *l2 = nullptr;
     if (which == SGSPM_M) {
         d0 = (T*)ctx->d_field[M1];
         d1 = (T*)ctx->d_field[M2];
         d2 = (T*)ctx->d_field[M3];
+        l0 = (T*)ctx->d_flo[M1];
+        l1 = (T*)ctx->d_flo[M2];
+        l2 = (T*)ctx->d_flo[M3];
     } else {
         // per-cell h_e is kept interleaved [cell][3]; stage through three scratch slots
         d0 = (T*)ctx->d_field[HS1];
         d1 = (T*)ctx->d_field[HS2];
         d2 = (T*)ctx->d_field[HS3];
-        (void)tmp;
     }
     if (dtype == SGSPM_F64_DATA)
-        copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, (const double*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+        copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const double*)ctx->d_stage,
+                                                               ctx->d_films, ctx->nfilm, n);
     else
-        copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, (const float*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+        copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const float*)ctx->d_stage,
+                                                              ctx->d_films, ctx->nfilm, n);
     CK(cudaGetLastError());
     if (which == SGSPM_M) {
         CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-        normalize_kernel<T><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, n, ctx->d_status);
+        normalize_kernel<T><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, n, ctx->d_status);
         CK(cudaGetLastError());
         int rc = check_status(ctx);
         if (rc) return fail(ctx, SGSPM_ERR_ARG, "set_field: zero-length or non-finite magnetisation vector");
@@ -818,10 +886,15 @@ static int get_field_t(sgspm_t ctx, int which, void* ptr, int dtype) {
     const T* s0 = (const T*)ctx->d_field[base];
     const T* s1 = (const T*)ctx->d_field[base + 1];
     const T* s2 = (const T*)ctx->d_field[base + 2];
+    const T* q0 = (const T*)ctx->d_flo[base];
+    const T* q1 = (const T*)ctx->d_flo[base + 1];
+    const T* q2 = (const T*)ctx->d_flo[base + 2];
     if (dtype == SGSPM_F64_DATA)
-        copy_out_kernel<T, double><<<nb, 256, 0, ctx->stream>>>((double*)ctx->d_stage, s0, s1, s2, ctx->d_films, ctx->nfilm, n);
+        copy_out_kernel<T, double><<<nb, 256, 0, ctx->stream>>>((double*)ctx->d_stage, s0, s1, s2, q0, q1, q2, ctx->d_films,
+                                                                ctx->nfilm, n);
     else
-        copy_out_kernel<T, float><<<nb, 256, 0, ctx->stream>>>((float*)ctx->d_stage, s0, s1, s2, ctx->d_films, ctx->nfilm, n);
+        copy_out_kernel<T, float><<<nb, 256, 0, ctx->stream>>>((float*)ctx->d_stage, s0, s1, s2, q0, q1, q2, ctx->d_films,
+                                                               ctx->nfilm, n);
     CK(cudaGetLastError());
     const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
     CK(cudaMemcpyAsync(ptr, ctx->d_stage, bytes, cudaMemcpyDefault, ctx->stream));

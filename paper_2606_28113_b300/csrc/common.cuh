@@ -33,6 +33,7 @@ struct Plan {
     int radix[kMaxStages];
     int tw;
     int tw4;
+    int dtab;   // offset of the dense DCT tables (P <= 16): C[k][n] then Ci[n][k]; -1 if none
 };
 
 // One film of a (possibly batched) handle.
@@ -109,12 +110,30 @@ struct Dev {
     const Plan* plans;
     const cplx<T>* tw;
     const T* lam;          // eigenvalue pool
+    const T* dtab;         // dense DCT tables of short axes
     const T* ktab;         // -N_hat / (Px Py Pz), reduced real table
     T* field[kMaxSlots];
+    T* flo[kMaxSlots];     // low parts of double-float state slots (FP32 form), else null
     cplx<T>* spec[kMaxSpec];
     const T* he_cell;      // per-cell applied field [3][ncell_total] or null
     int* status;
     const long long* step_ctr;
 };
+
+// ---- error-free transformations (FP32 double-float arithmetic of the state) -----------------
+// Knuth's two-sum, Dekker's fast two-sum and the FMA two-product.
+template <typename T> __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+    s = a + b;
+    T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+template <typename T> __device__ __forceinline__ void fast_two_sum(T a, T b, T& s, T& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+template <typename T> __device__ __forceinline__ void two_prod(T a, T b, T& p, T& e) {
+    p = a * b;
+    e = fma(a, b, -p);
+}
 
 }  // namespace sgspm

@@ -68,6 +68,42 @@ template <bool INV, typename V> struct Bfly<8, INV, V> {
     }
 };
 
+template <bool INV, typename V> struct Bfly<16, INV, V> {
+    // 16 = 4 x 4: DFT4 over m of a[r + 4m], twiddle W16^{rs}, DFT4 over r; X[s + 4t]
+    static __device__ __forceinline__ void run(V* a) {
+        using T = decltype(V::x);
+        const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), h = T(0.70710678118654752440);
+        V b[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            V q[4] = {a[r], a[r + 4], a[r + 8], a[r + 12]};
+            Bfly<4, INV, V>::run(q);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) b[r][s] = q[s];
+        }
+        // W16^k = (cos(2 pi k/16), -+ sin(2 pi k/16)) for k = r*s in {1,2,3,4,6,9}
+        const T sg = INV ? T(1) : T(-1);
+        const V w1 = cmk<V>(c1, sg * s1), w2 = cmk<V>(h, sg * h), w3 = cmk<V>(s1, sg * c1);
+        const V w6 = cmk<V>(-h, sg * h), w9 = cmk<V>(-c1, -sg * s1);
+        b[1][1] = cmul(b[1][1], w1);
+        b[1][2] = cmul(b[1][2], w2);
+        b[1][3] = cmul(b[1][3], w3);
+        b[2][1] = cmul(b[2][1], w2);
+        b[2][2] = rot_i<INV>(b[2][2]);
+        b[2][3] = cmul(b[2][3], w6);
+        b[3][1] = cmul(b[3][1], w3);
+        b[3][2] = cmul(b[3][2], w6);
+        b[3][3] = cmul(b[3][3], w9);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            V q[4] = {b[0][s], b[1][s], b[2][s], b[3][s]};
+            Bfly<4, INV, V>::run(q);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) a[s + 4 * t] = q[t];
+        }
+    }
+};
+
 template <bool INV, typename V> struct Bfly<3, INV, V> {
     static __device__ __forceinline__ void run(V* a) {
         using T = decltype(V::x);
@@ -133,11 +169,228 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, 
     }
 }
 
+// ---- compile-time Stockham for power-of-two lengths: all index arithmetic folds to shifts ----
+template <typename T, bool INV, int P, int R, int NS, bool CONTIG>
+__device__ __forceinline__ void ct_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, Lines L,
+                                         const cplx<T>* __restrict__ tw) {
+    using V = cplx<T>;
+    constexpr int NB = P / R;
+    constexpr int TWS = P / (NS * R);
+    const int total = L.n * NB;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int line, j;
+        if (CONTIG) { line = idx / NB; j = idx % NB; }
+        else { j = idx / L.n; line = idx - j * L.n; }
+        const int es = CONTIG ? 1 : L.es;
+        const V* s = src + (long)line * L.ls;
+        V* d = dst + (long)line * L.ls;
+        const int k = j % NS;
+        V v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = s[(j + t * NB) * es];
+        if (NS > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                V w = tw[k * t * TWS];
+                if (INV) w = cconj(w);
+                v[t] = cmul(v[t], w);
+            }
+        }
+        Bfly<R, INV, V>::run(v);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) d[(base + t * NS) * es] = v[t];
+    }
+}
+
+__host__ __device__ constexpr int ct_radix(int rem) { return rem % 16 == 0 ? 16 : rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : 2; }
+
+template <typename T, bool INV, int P, int NS, bool CONTIG>
+struct CtFFT {
+    static __device__ __forceinline__ cplx<T>* run(cplx<T>* a, cplx<T>* b, Lines L, const cplx<T>* tw) {
+        constexpr int R = ct_radix(P / NS);
+        ct_stage<T, INV, P, R, NS, CONTIG>(a, b, L, tw);
+        __syncthreads();
+        return CtFFT<T, INV, P, NS * R, CONTIG>::run(b, a, L, tw);
+    }
+};
+template <typename T, bool INV, int P, bool CONTIG>
+struct CtFFT<T, INV, P, P, CONTIG> {
+    static __device__ __forceinline__ cplx<T>* run(cplx<T>* a, cplx<T>*, Lines, const cplx<T>*) { return a; }
+};
+
+template <typename T, bool INV, int P>
+__device__ __forceinline__ cplx<T>* ct_fft(cplx<T>* a, cplx<T>* b, Lines L, const cplx<T>* tw) {
+    if (L.es == 1) return CtFFT<T, INV, P, 1, true>::run(a, b, L, tw);
+    return CtFFT<T, INV, P, 1, false>::run(a, b, L, tw);
+}
+
+// ---- warp-per-line FFT, P = 32 E (E = 2..16), natural order in and out --------------------------
+// Lane j holds x[j + 32k] (k < E): E-point DFT in registers, twiddle W_P^{jq}; one transpose through
+// the line's scratch region (XOR swizzle, conflict-free); lane (q, g) (G = 32/E lanes per q) takes
+// y_{g + G i}[q], E-point DFT over i, twiddle W_32^{g s1}, then a G-point DIF across the G lanes by
+// shuffles, which leaves X[q + E (s1 + E bitrev(g))] in lane (q, g).  Only __syncwarp inside.
+template <typename T, bool INV, int E>
+__device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* __restrict__ scr,
+                                              const cplx<T>* __restrict__ tw, int lane) {
+    using V = cplx<T>;
+    constexpr int P = 32 * E, G = 32 / E;
+    V v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) v[k] = a[lane + 32 * k];
+    Bfly<E, INV, V>::run(v);
+#pragma unroll
+    for (int q = 1; q < E; ++q) {
+        V w = tw[lane * q];
+        if (INV) w = cconj(w);
+        v[q] = cmul(v[q], w);
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) scr[q * 32 + (lane ^ ((q * G) & 31))] = v[q];
+    __syncwarp();
+    const int q = lane / G, g = lane % G;
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = scr[q * 32 + ((g + G * i) ^ ((q * G) & 31))];
+    Bfly<E, INV, V>::run(v);
+    if (G > 1) {
+#pragma unroll
+        for (int s1 = 1; s1 < E; ++s1) {
+            V w = tw[E * g * s1];
+            if (INV) w = cconj(w);
+            v[s1] = cmul(v[s1], w);
+        }
+    }
+#pragma unroll
+    for (int d = G / 2; d >= 1; d >>= 1) {
+        const bool top = (g & d) == 0;
+        V w = tw[(P / (2 * d)) * (g % d)];
+        if (INV) w = cconj(w);
+#pragma unroll
+        for (int s1 = 0; s1 < E; ++s1) {
+            V pv;
+            pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
+            pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
+            v[s1] = top ? cadd(v[s1], pv) : cmul(csub(pv, v[s1]), w);
+        }
+    }
+    const int s2 = G > 1 ? (int)(__brev((unsigned)g) >> (32 - __ffs(G) + 1)) : 0;
+#pragma unroll
+    for (int s1 = 0; s1 < E; ++s1) a[q + E * (s1 + E * s2)] = v[s1];
+}
+
+// Register-resident forward FFT of one line held by a warp: on entry v[k] = x[lane + 32k];
+// on exit v[s1] = X[q + E (s1 + E bitrev_G(g))] with q = lane / G, g = lane % G.
+template <typename T, int E>
+__device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const cplx<T>* __restrict__ tw, int lane) {
+    using V = cplx<T>;
+    constexpr int P = 32 * E, G = 32 / E;
+    Bfly<E, false, V>::run(v);
+#pragma unroll
+    for (int q = 1; q < E; ++q) v[q] = cmul(v[q], tw[lane * q]);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < E; ++q) scr[q * 32 + (lane ^ ((q * G) & 31))] = v[q];
+    __syncwarp();
+    const int q = lane / G, g = lane % G;
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = scr[q * 32 + ((g + G * i) ^ ((q * G) & 31))];
+    Bfly<E, false, V>::run(v);
+    if (G > 1) {
+#pragma unroll
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], tw[E * g * s1]);
+    }
+#pragma unroll
+    for (int d = G / 2; d >= 1; d >>= 1) {
+        const bool top = (g & d) == 0;
+        const V w = tw[(P / (2 * d)) * (g % d)];
+#pragma unroll
+        for (int s1 = 0; s1 < E; ++s1) {
+            V pv;
+            pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
+            pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
+            v[s1] = top ? cadd(v[s1], pv) : cmul(csub(pv, v[s1]), w);
+        }
+    }
+}
+
+// The adjoint of wreg_fwd: from the scrambled order back to v[k] = P * IDFT(X)[lane + 32k].
+template <typename T, int E>
+__device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const cplx<T>* __restrict__ tw, int lane) {
+    using V = cplx<T>;
+    constexpr int P = 32 * E, G = 32 / E;
+    const int q = lane / G, g = lane % G;
+#pragma unroll
+    for (int d = 1; d <= G / 2; d <<= 1) {
+        const bool top = (g & d) == 0;
+        const V w = cconj(tw[(P / (2 * d)) * (g % d)]);
+#pragma unroll
+        for (int s1 = 0; s1 < E; ++s1) {
+            V pv;
+            pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
+            pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
+            v[s1] = top ? cadd(v[s1], cmul(w, pv)) : csub(pv, cmul(w, v[s1]));
+        }
+    }
+    if (G > 1) {
+#pragma unroll
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], cconj(tw[E * g * s1]));
+    }
+    Bfly<E, true, V>::run(v);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < E; ++i) scr[q * 32 + ((g + G * i) ^ ((q * G) & 31))] = v[i];
+    __syncwarp();
+#pragma unroll
+    for (int qq = 0; qq < E; ++qq) v[qq] = scr[qq * 32 + (lane ^ ((qq * G) & 31))];
+#pragma unroll
+    for (int qq = 1; qq < E; ++qq) v[qq] = cmul(v[qq], cconj(tw[lane * qq]));
+    Bfly<E, true, V>::run(v);
+}
+
+__device__ __forceinline__ int bitrev_lanes(int g, int G) {
+    return G > 1 ? (int)(__brev((unsigned)g) >> (33 - __ffs(G))) : 0;
+}
+
+template <typename T, bool INV, int E>
+__device__ __forceinline__ cplx<T>* warp_fft(cplx<T>* a, cplx<T>* b, Lines L, const cplx<T>* tw) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int line = threadIdx.x >> 5; line < L.n; line += nw)
+        warp_fft_line<T, INV, E>(a + (long)line * L.ls, b + (long)line * L.ls, tw, lane);
+    __syncthreads();
+    return a;
+}
+
 // Full FFT of all lines.  Data starts in `a`; `b` is scratch of the same shape.  Returns the
-// buffer holding the result (a or b).  Unnormalised in both directions.
+// buffer holding the result (a or b).  Unnormalised in both directions.  Contiguous lines of
+// length 64..512 use the warp-per-line FFT; other power-of-two lengths up to 2048 the
+// compile-time Stockham; other lengths the generic mixed-radix Stockham.
 template <typename T, bool INV>
 __device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, const cplx<T>* __restrict__ twpool) {
     const cplx<T>* tw = twpool + pl.tw;
+    if (L.es == 1 && L.ls >= pl.P) {
+        switch (pl.P) {
+            case 64: return warp_fft<T, INV, 2>(a, b, L, tw);
+            case 128: return warp_fft<T, INV, 4>(a, b, L, tw);
+            case 256: return warp_fft<T, INV, 8>(a, b, L, tw);
+            case 512: return warp_fft<T, INV, 16>(a, b, L, tw);
+            default: break;
+        }
+    }
+    switch (pl.P) {
+        case 1: return a;
+        case 2: return ct_fft<T, INV, 2>(a, b, L, tw);
+        case 4: return ct_fft<T, INV, 4>(a, b, L, tw);
+        case 8: return ct_fft<T, INV, 8>(a, b, L, tw);
+        case 16: return ct_fft<T, INV, 16>(a, b, L, tw);
+        case 32: return ct_fft<T, INV, 32>(a, b, L, tw);
+        case 64: return ct_fft<T, INV, 64>(a, b, L, tw);
+        case 128: return ct_fft<T, INV, 128>(a, b, L, tw);
+        case 256: return ct_fft<T, INV, 256>(a, b, L, tw);
+        case 512: return ct_fft<T, INV, 512>(a, b, L, tw);
+        case 1024: return ct_fft<T, INV, 1024>(a, b, L, tw);
+        case 2048: return ct_fft<T, INV, 2048>(a, b, L, tw);
+        default: break;
+    }
     int Ns = 1;
     for (int s = 0; s < pl.nst; ++s) {
         const int r = pl.radix[s];

@@ -158,16 +158,22 @@ __global__ void newell_axis_kernel(const double* __restrict__ in, double* __rest
     out[c * out_sc + i2 * out_s2 + i1 * out_s1 + k * out_s_elem] = s;
 }
 
-// ktab[c][kz][ky][kx] = -(+-) N_hat / (Px Py Pz): the two odd axes of an off-diagonal
-// component contribute (-i)^2 = -1.
+// ktab[c][kz][kx][ky] = -(+-) N_hat / (Px Py Pz) from nhat[c][kz][ky][kx]: the two odd axes
+// of an off-diagonal component contribute (-i)^2 = -1.
 template <typename T>
-__global__ void newell_finish_kernel(const double* __restrict__ nhat, T* __restrict__ ktab, long long n6, double scale) {
+__global__ void newell_finish_kernel(const double* __restrict__ nhat, T* __restrict__ ktab, int Kx, int Hy, int Hz, double scale) {
     long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n6 = (long long)Hz * Hy * Kx;
     if (id >= 6 * n6) return;
-    int c = id / n6;
+    const int c = (int)(id / n6);
+    long long r = id - c * n6;
+    const int kx = (int)(r % Kx);
+    r /= Kx;
+    const int ky = (int)(r % Hy);
+    const int kz = (int)(r / Hy);
     double v = nhat[id];
     if (c >= 3) v = -v;
-    ktab[id] = (T)(-v * scale);
+    ktab[ktab_index(c, kx, kz, ky, Kx, Hy, Hz)] = (T)(-v * scale);
 }
 
 }  // namespace sgspm

@@ -40,7 +40,7 @@ __device__ inline void mms_forcing(int dim, double x, double y, double z, double
 // XZ slab pass
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
+__global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int4 wi = work[blockIdx.x];
@@ -48,17 +48,6 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
     const int y = wi.y;
     const int nx = F.nx, ny = F.ny, nz = F.nz, Px = F.Px, Pz = F.Pz, Kx = F.Kx;
     const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0);
-    V* xw0 = reinterpret_cast<V*>(smem_raw);
-    V* xw1 = xw0 + Lo.xw;
-    V* zw0 = xw1 + Lo.xw;
-    V* zw1 = zw0 + Lo.zw;
-    T* slabs = reinterpret_cast<T*>(zw1 + Lo.zw);
-    const int S = Lo.slab;
-    const int KC = Lo.kc;
-    const int npx = (nz + 1) / 2;
-    const int nxz = nx * nz;
-    const long long cbase = F.off_cell;
-    const long long sbase = F.off_spec;
     __shared__ Plan pdx, pdz, ppx, ppz;
     if (threadIdx.x == 0) {
         pdx = d.plans[F.plan_dx];
@@ -67,7 +56,43 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
         ppz = d.plans[F.plan_pz];
     }
     __syncthreads();
+    // staged twiddles: [W_nx | W4_nx | W_nz | W4_nz | W_Px | W_Pz], then the short-axis DCT tables
+    V* stw = reinterpret_cast<V*>(smem_raw);
+    stage_plan<T>(pdx, d.tw, stw, 0, true);
+    stage_plan<T>(pdz, d.tw, stw, 2 * nx, true);
+    if (stray) {
+        stage_plan<T>(ppx, d.tw, stw, 2 * nx + 2 * nz, false);
+        stage_plan<T>(ppz, d.tw, stw, 2 * nx + 2 * nz + Px, false);
+    }
+    V* xw0 = stw + Lo.tw;
+    V* xw1 = xw0 + Lo.xw;
+    V* zw0 = xw1 + Lo.xw;
+    V* zw1 = zw0 + Lo.zw;
+    T* slabs = reinterpret_cast<T*>(zw1 + Lo.zw);
+    T* sdt = slabs + 3 * Lo.slab;
+    if (Lo.dt)
+        for (int i = threadIdx.x; i < 2 * nz * nz; i += blockDim.x) sdt[i] = d.dtab[pdz.dtab + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        pdx.tw = 0;
+        pdx.tw4 = nx;
+        pdz.tw = 2 * nx;
+        pdz.tw4 = 2 * nx + nz;
+        ppx.tw = 2 * nx + 2 * nz;
+        ppz.tw = 2 * nx + 2 * nz + Px;
+    }
+    __syncthreads();
+    const int S = Lo.slab;
+    const int KC = Lo.kc;
+    const int npx = (nz + 1) / 2;
+    const int nxz = nx * nz;
+    const long long cbase = F.off_cell;
+    const long long sbase = F.off_spec;
     auto cell_of = [&](int z, int x) -> long long { return cbase + ((long long)z * ny + y) * nx + x; };
+    const bool zreg = z_in_registers(nz);
+    const T* Cz = sdt;                                       // DCT-II  C[k][n]
+    const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
+    const V* twz = stw + ppz.tw;                             // W_Pz^m
 
     // ---- phase R: right-hand sides and forward DCT ---------------------------------------
     for (int ci = 0; ci < pg.n_rhs; ++ci) {
@@ -75,14 +100,42 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
         T* h = slabs;   // slab 0
         if (pg.rhs_h[ci] >= 0 && stray) {
             const V* H = d.spec[pg.rhs_h[ci]] + sbase;
-            for (int kc0 = 0; kc0 < Kx; kc0 += KC) {
+            if (zreg) {
+                // inverse zero-padded DFT along z in registers, one thread per kx column
+                for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
+                    V acc[kZReg];
+#pragma unroll
+                    for (int z = 0; z < kZReg; ++z) acc[z] = cmk<V>(T(0), T(0));
+                    V hz[2 * kZReg];
+#pragma unroll
+                    for (int kz = 0; kz < 2 * kZReg; ++kz)
+                        hz[kz] = kz < Pz ? H[((long long)kz * ny + y) * Kx + kx] : cmk<V>(T(0), T(0));
+#pragma unroll
+                    for (int kz = 0; kz < 2 * kZReg; ++kz) {
+                        if (kz >= Pz) break;
+                        const V hv = hz[kz];
+                        int m = 0;
+#pragma unroll
+                        for (int z = 0; z < kZReg; ++z) {
+                            if (z < nz) acc[z] = cadd(acc[z], cmul(hv, cconj(twz[m])));
+                            m += kz;
+                            if (m >= Pz) m -= Pz;
+                        }
+                    }
+#pragma unroll
+                    for (int p = 0; p < kZReg / 2; ++p)
+                        if (2 * p < nz) c2r_put<T>(xw0, p, kx, Px, acc[2 * p], (2 * p + 1 < nz) ? acc[2 * p + 1] : cmk<V>(T(0), T(0)));
+                }
+                __syncthreads();
+            }
+            for (int kc0 = 0; !zreg && kc0 < Kx; kc0 += KC) {
                 const int kcn = min(KC, Kx - kc0);
                 for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
                     int kz = idx / kcn, kc = idx - kz * kcn;
                     zw0[kz * KC + kc] = H[((long long)kz * ny + y) * Kx + kc0 + kc];
                 }
                 __syncthreads();
-                V* r = fft_lines<T, true>(zw0, zw1, Lines{kcn, 1, KC}, ppz, d.tw);
+                V* r = fft_lines<T, true>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
                 for (int idx = threadIdx.x; idx < npx * kcn; idx += blockDim.x) {
                     int p = idx / kcn, kc = idx - p * kcn;
                     V xa = r[(2 * p) * KC + kc];
@@ -91,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
                 }
                 __syncthreads();
             }
-            V* r = fft_lines<T, true>(xw0, xw1, Lines{npx, Px, 1}, ppx, d.tw);
+            V* r = fft_lines<T, true>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
                 int z = idx / nx, x = idx - z * nx;
                 V v = r[(z >> 1) * Px + x];
@@ -111,37 +164,57 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
         if (!pg.rhs_dct) { __syncthreads(); continue; }
         // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
         {
-            const T* m1 = d.field[pg.state[0]];
-            const T* m2 = d.field[pg.state[1]];
-            const T* m3 = d.field[pg.state[2]];
-            const T* ma = d.field[pg.state[a]];
+            const T* __restrict__ m1 = d.field[pg.state[0]];
+            const T* __restrict__ m2 = d.field[pg.state[1]];
+            const T* __restrict__ m3 = d.field[pg.state[2]];
+            const T* __restrict__ ma = d.field[pg.state[a]];
+            const T* __restrict__ ml = d.flo[pg.state[a]];   // low part (double-float state) or null
             const T scale = T(pg.damp ? F.alpha * F.dt : F.dt);
             const T eps = T(F.eps), Q = T(F.Q);
             const T ux = T(F.u[0]), uy = T(F.u[1]), uz = T(F.u[2]);
             const T ua = T(F.u[a]);
             const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
             const T hea = T(F.he[a]);
+            const long long sz = (long long)nx * ny;
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                int z = idx / nx, x = idx - z * nx;
-                long long c = cell_of(z, x);
-                T v1 = m1[c], v2 = m2[c], v3 = m3[c];
-                T mc = ma[c];
-                T mu = v1 * ux + v2 * uy + v3 * uz;
+                const int z = idx / nx, x = idx - z * nx;
+                const long long c = cell_of(z, x);
+                const T v1 = m1[c], v2 = m2[c], v3 = m3[c];
+                const T mc = ma[c];
+                const T mcl = ml ? ml[c] : T(0);
+                const T mu = v1 * ux + v2 * uy + v3 * uz;
+                // mirror ghosts: a missing neighbour contributes a zero difference
+                auto dif = [&](long long o) -> T { return (ma[c + o] - mc) + (ml ? ml[c + o] - mcl : T(0)); };
                 T lap = T(0);
-                if (nx > 1) lap += ihx * ((x + 1 < nx ? ma[c + 1] : mc) - T(2) * mc + (x > 0 ? ma[c - 1] : mc));
-                if (ny > 1) lap += ihy * ((y + 1 < ny ? ma[c + nx] : mc) - T(2) * mc + (y > 0 ? ma[c - nx] : mc));
-                if (nz > 1) {
-                    long long sz = (long long)nx * ny;
-                    lap += ihz * ((z + 1 < nz ? ma[c + sz] : mc) - T(2) * mc + (z > 0 ? ma[c - sz] : mc));
-                }
-                T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
-                T f = -Q * (mc - mu * ua) + h[idx] + he;
+                if (nx > 1) lap += ihx * ((x + 1 < nx ? dif(1) : T(0)) + (x > 0 ? dif(-1) : T(0)));
+                if (ny > 1) lap += ihy * ((y + 1 < ny ? dif(nx) : T(0)) + (y > 0 ? dif(-nx) : T(0)));
+                if (nz > 1) lap += ihz * ((z + 1 < nz ? dif(sz) : T(0)) + (z > 0 ? dif(-sz) : T(0)));
+                const T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
+                const T f = -Q * (mc - mu * ua) + h[idx] + he;
                 h[idx] = scale * (f + eps * lap);
             }
         }
         __syncthreads();
-        dct2_lines<T>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, d.tw);
-        dct2_lines<T>(h, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, d.tw);
+        dct2_lines<T>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
+        if (zreg) {
+            for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+                T v[kZReg];
+#pragma unroll
+                for (int z = 0; z < kZReg; ++z) v[z] = z < nz ? h[z * nx + x] : T(0);
+#pragma unroll
+                for (int k = 0; k < kZReg; ++k) {
+                    if (k >= nz) break;
+                    T acc = T(0);
+#pragma unroll
+                    for (int z = 0; z < kZReg; ++z)
+                        if (z < nz) acc += Cz[k * nz + z] * v[z];
+                    h[k * nx + x] = acc;
+                }
+            }
+            __syncthreads();
+        } else {
+            dct2_lines<T>(h, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
+        }
         {
             T* out = d.field[pg.rhs_out[ci]];
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
@@ -161,8 +234,26 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
             s[idx] = in[cell_of(z, x)];
         }
         __syncthreads();
-        dct3_lines<T>(s, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, d.tw);
-        dct3_lines<T>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, d.tw);
+        if (zreg) {
+            for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+                T v[kZReg];
+#pragma unroll
+                for (int k = 0; k < kZReg; ++k) v[k] = k < nz ? s[k * nx + x] : T(0);
+#pragma unroll
+                for (int z = 0; z < kZReg; ++z) {
+                    if (z >= nz) break;
+                    T acc = T(0);
+#pragma unroll
+                    for (int k = 0; k < kZReg; ++k)
+                        if (k < nz) acc += Czi[z * nz + k] * v[k];
+                    s[z * nx + x] = acc;
+                }
+            }
+            __syncthreads();
+        } else {
+            dct3_lines<T>(s, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
+        }
+        dct3_lines<T>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
         if (pg.inv_store[i] >= 0) {
             T* out = d.field[pg.inv_store[i]];
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
@@ -176,7 +267,11 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
     if (pg.op == 1) {
         // Gauss-Seidel cross product: out = base + p*q - r*s  (delta form, see host program)
         T* out = d.field[pg.gs_out];
+        T* outl = d.flo[pg.gs_out];
         T* res = slabs + 2 * S;
+        const T* bl_ = pg.gs_base >= 0 ? d.flo[pg.gs_base] : nullptr;
+        const T* ql_ = pg.gs_q >= 0 ? d.flo[pg.gs_q] : nullptr;
+        const T* sl_ = pg.gs_s >= 0 ? d.flo[pg.gs_s] : nullptr;
         for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
             int z = idx / nx, x = idx - z * nx;
             long long c = cell_of(z, x);
@@ -185,17 +280,84 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
             T q = load_ref(d, pg.gs_q, c, slabs, S, idx);
             T r = load_ref(d, pg.gs_r, c, slabs, S, idx);
             T s = load_ref(d, pg.gs_s, c, slabs, S, idx);
-            T v = b + (p * q - r * s);
-            out[c] = v;
-            res[idx] = v;
+            if (outl) {
+                // double-float state: base (hi, lo) + increment p (q_hi + q_lo) - r (s_hi + s_lo)
+                const T ql = ql_ ? ql_[c] : T(0), sl = sl_ ? sl_[c] : T(0), bl = bl_ ? bl_[c] : T(0);
+                const T rs = fma(r, sl, r * s);
+                const T inc = fma(p, q, fma(p, ql, -rs));
+                T hi, e;
+                two_sum(b, inc, hi, e);
+                T h2, l2;
+                fast_two_sum(hi, e + bl, h2, l2);
+                out[c] = h2;
+                outl[c] = l2;
+                res[idx] = h2;
+            } else {
+                T v = b + (p * q - r * s);
+                out[c] = v;
+                res[idx] = v;
+            }
         }
         __syncthreads();
     } else if (pg.op == 2) {
         // Step 2 + Step 3: m*** = m** + delta (+ dt f_e), m^{n+1} = m*** / |m***|
         const double tnow = F.t0 + (double)(*d.step_ctr) * F.dt;
+        const bool dfl = d.flo[pg.fin_out[0]] != nullptr;
         for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
             int z = idx / nx, x = idx - z * nx;
             long long c = cell_of(z, x);
+            if (dfl) {
+                // m*** = m** + delta in double-float, then |m***|^-1 by one double-float Newton step
+                T h[3], l[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    T s1, e1;
+                    two_sum(d.field[pg.fin_in[i]][c], slabs[i * S + idx], s1, e1);
+                    fast_two_sum(s1, e1 + d.flo[pg.fin_in[i]][c], h[i], l[i]);
+                }
+                if (F.forcing) {
+                    double fe[3];
+                    mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        double v = (double)h[i] + (double)l[i] + F.dt * fe[i];
+                        h[i] = (T)v;
+                        l[i] = (T)(v - (double)h[i]);
+                    }
+                }
+                T p0, e0, p1, e1, p2, e2;
+                two_prod(h[0], h[0], p0, e0);
+                two_prod(h[1], h[1], p1, e1);
+                two_prod(h[2], h[2], p2, e2);
+                T s1, f1, n2h, f2;
+                two_sum(p0, p1, s1, f1);
+                two_sum(s1, p2, n2h, f2);
+                T n2l = f1 + f2 + e0 + e1 + e2 + T(2) * (h[0] * l[0] + h[1] * l[1] + h[2] * l[2]);
+                T nh, nl;
+                fast_two_sum(n2h, n2l, nh, nl);
+                if (!(nh > T(0)) || !isfinite(nh)) {
+                    atomicOr(d.status, 1);
+                    nh = T(1);
+                    nl = T(0);
+                }
+                const T r0 = rsqrt(nh);
+                T q, qe, a, ae;
+                two_prod(r0, r0, q, qe);
+                two_prod(nh, q, a, ae);
+                const T rho = ((T(1) - a) - ae) - (nh * qe + nl * q);
+                const T cc = T(0.5) * r0 * rho;                  // 1/|m***| = r0 + cc
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    T pp, pe;
+                    two_prod(h[i], r0, pp, pe);
+                    T oh, ol;
+                    fast_two_sum(pp, pe + (h[i] * cc + l[i] * r0), oh, ol);
+                    d.field[pg.fin_out[i]][c] = oh;
+                    d.flo[pg.fin_out[i]][c] = ol;
+                    slabs[i * S + idx] = oh;
+                }
+                continue;
+            }
             T v[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) v[i] = d.field[pg.fin_in[i]][c] + slabs[i * S + idx];
@@ -238,16 +400,36 @@ __global__ void __launch_bounds__(kThreads) xz_kernel(Dev<T> d, const int4* __re
             } else {
                 src = slabs + (-1 - ref) * S;
             }
-            V* r = r2c_lines<T>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, d.tw);
+            V* r = r2c_lines<T>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
             V* out = d.spec[pg.fwd_dst[i]] + sbase;
-            for (int kc0 = 0; kc0 < Kx; kc0 += KC) {
+            if (zreg) {
+                // zero-padded DFT along z in registers, one thread per kx column
+                for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
+                    V v[kZReg];
+#pragma unroll
+                    for (int z = 0; z < kZReg; ++z) v[z] = z < nz ? r2c_get<T>(r, z, kx, Px) : cmk<V>(T(0), T(0));
+                    for (int kz = 0; kz < Pz; ++kz) {
+                        V acc = cmk<V>(T(0), T(0));
+                        int m = 0;
+#pragma unroll
+                        for (int z = 0; z < kZReg; ++z) {
+                            if (z < nz) acc = cadd(acc, cmul(v[z], twz[m]));
+                            m += kz;
+                            if (m >= Pz) m -= Pz;
+                        }
+                        out[((long long)kz * ny + y) * Kx + kx] = acc;
+                    }
+                }
+                __syncthreads();
+            }
+            for (int kc0 = 0; !zreg && kc0 < Kx; kc0 += KC) {
                 const int kcn = min(KC, Kx - kc0);
                 for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
                     int z = idx / kcn, kc = idx - z * kcn;
                     zw0[z * KC + kc] = (z < nz) ? r2c_get<T>(r, z, kc0 + kc, Px) : cmk<V>(T(0), T(0));
                 }
                 __syncthreads();
-                V* q = fft_lines<T, false>(zw0, zw1, Lines{kcn, 1, KC}, ppz, d.tw);
+                V* q = fft_lines<T, false>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
                 for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
                     int kz = idx / kcn, kc = idx - kz * kcn;
                     out[((long long)kz * ny + y) * Kx + kc0 + kc] = q[kz * KC + kc];
@@ -272,10 +454,19 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
     __shared__ Plan pdy;
     if (threadIdx.x == 0) pdy = d.plans[F.plan_dy];
     __syncthreads();
+    V* stw = reinterpret_cast<V*>(smem_raw);
+    stage_plan<T>(pdy, d.tw, stw, 0, true);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        pdy.tw = 0;
+        pdy.tw4 = ny;
+    }
+    __syncthreads();
     const int npair = (tn + 1) / 2;
-    V* c0 = reinterpret_cast<V*>(smem_raw);
+    V* c0 = stw + 2 * ny;
     V* c1 = c0 + npair * ny;
     T* R = reinterpret_cast<T*>(c1 + npair * ny);
+    const int LR = ny + 8;   // padded line stride: tile copies hit distinct banks
     const T c = T(pg.damp ? F.alpha * F.eps : F.eps) * T(F.dt);
     const T* lx = d.lam + F.lam;
     const T* ly = lx + nx;
@@ -285,19 +476,19 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
         T* g = d.field[pg.slot[f]] + F.off_cell + (long long)kz * ny * nx + kx0;
         for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
             int yy = idx / tn, t = idx - yy * tn;
-            R[t * ny + yy] = g[(long long)yy * nx + t];
+            R[t * LR + yy] = g[(long long)yy * nx + t];
         }
         __syncthreads();
-        dct2_lines<T>(R, Lines{tn, ny, 1}, ny, c0, c1, pdy, d.tw);
+        dct2_lines<T>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
         for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
             int t = idx / ny, ky = idx - t * ny;
-            R[idx] *= norm / (T(1) + c * (lx[kx0 + t] + ly[ky] + lzv));
+            R[t * LR + ky] *= norm / (T(1) + c * (lx[kx0 + t] + ly[ky] + lzv));
         }
         __syncthreads();
-        dct3_lines<T>(R, Lines{tn, ny, 1}, ny, c0, c1, pdy, d.tw);
+        dct3_lines<T>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
         for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
             int yy = idx / tn, t = idx - yy * tn;
-            g[(long long)yy * nx + t] = R[t * ny + yy];
+            g[(long long)yy * nx + t] = R[t * LR + yy];
         }
         __syncthreads();
     }
@@ -321,8 +512,14 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
     __shared__ Plan ppy;
     if (threadIdx.x == 0) ppy = d.plans[F.plan_py];
     __syncthreads();
-    const int B = tx * Py;
-    V* w0 = reinterpret_cast<V*>(smem_raw);
+    V* stw = reinterpret_cast<V*>(smem_raw);
+    stage_plan<T>(ppy, d.tw, stw, 0, false);
+    __syncthreads();
+    if (threadIdx.x == 0) ppy.tw = 0;
+    __syncthreads();
+    const int LS = Py + 4;   // padded line stride: tile copies hit distinct banks
+    const int B = tx * LS;
+    V* w0 = stw + Py;
     V* w1 = w0 + B;
     V* acc = w1 + B;     // pg.n accumulators
     const int Hy = Py / 2 + 1, Hz = Pz / 2 + 1;
@@ -330,41 +527,155 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
     const bool zodd = kz > Pz / 2;
     const T* kt = d.ktab + F.off_ktab;
     for (int o = 0; o < pg.n; ++o)
-        for (int idx = threadIdx.x; idx < tn * Py; idx += blockDim.x) acc[o * B + idx] = cmk<V>(T(0), T(0));
+        for (int idx = threadIdx.x; idx < tn * LS; idx += blockDim.x) acc[o * B + idx] = cmk<V>(T(0), T(0));
     for (int b = 0; b < 3; ++b) {
         const V* Sb = d.spec[pg.in_spec[b]] + F.off_spec + (long long)kz * ny * Kx + kx0;
         for (int idx = threadIdx.x; idx < tn * Py; idx += blockDim.x) {
             int yy = idx / tn, t = idx - yy * tn;
-            w0[t * Py + yy] = (yy < ny) ? Sb[(long long)yy * Kx + t] : cmk<V>(T(0), T(0));
+            w0[t * LS + yy] = (yy < ny) ? Sb[(long long)yy * Kx + t] : cmk<V>(T(0), T(0));
         }
         __syncthreads();
-        V* M = fft_lines<T, false>(w0, w1, Lines{tn, Py, 1}, ppy, d.tw);
-        for (int idx = threadIdx.x; idx < tn * Py; idx += blockDim.x) {
-            int t = idx / Py, ky = idx - t * Py;
-            const int kyr = ky <= Py - ky ? ky : Py - ky;
-            const bool yodd = ky > Py / 2;
-            V m = M[idx];
-            for (int o = 0; o < pg.n; ++o) {
-                const int a = pg.slot[o];
-                const int cc = pair_idx(a, b);
-                T k = kt[ktab_index(cc, kx0 + t, kzr, kyr, Kx, Hy, Hz)];
-                bool neg = ((cc == 3 || cc == 5) && yodd) != ((cc == 4 || cc == 5) && zodd);
-                if (neg) k = -k;
-                V& A = acc[o * B + idx];
-                A.x += k * m.x;
-                A.y += k * m.y;
+        V* M = fft_lines<T, false>(w0, w1, Lines{tn, LS, 1}, ppy, stw);
+        // spectral multiply: issue all table loads of a batch before the accumulations
+        const int total = tn * Py;
+        for (int base = threadIdx.x; base < total; base += 4 * blockDim.x) {
+            T kv[4][3];
+            int ids[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * blockDim.x;
+                ids[u] = idx;
+                if (idx < total) {
+                    const int t = idx / Py, ky = idx - t * Py;
+                    const int kyr = ky <= Py - ky ? ky : Py - ky;
+                    const bool yodd = ky > Py / 2;
+#pragma unroll
+                    for (int o = 0; o < 3; ++o) {
+                        if (o < pg.n) {
+                            const int cc = pair_idx(pg.slot[o], b);
+                            T k = kt[ktab_index(cc, kx0 + t, kzr, kyr, Kx, Hy, Hz)];
+                            const bool neg = ((cc == 3 || cc == 5) && yodd) != ((cc == 4 || cc == 5) && zodd);
+                            kv[u][o] = neg ? -k : k;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = ids[u];
+                if (idx < total) {
+                    const int li = (idx / Py) * LS + (idx % Py);
+                    const V m = M[li];
+#pragma unroll
+                    for (int o = 0; o < 3; ++o) {
+                        if (o < pg.n) {
+                            V& A = acc[o * B + li];
+                            A.x += kv[u][o] * m.x;
+                            A.y += kv[u][o] * m.y;
+                        }
+                    }
+                }
             }
         }
         __syncthreads();
     }
     for (int o = 0; o < pg.n; ++o) {
-        V* r = fft_lines<T, true>(acc + o * B, w0, Lines{tn, Py, 1}, ppy, d.tw);
+        V* r = fft_lines<T, true>(acc + o * B, w0, Lines{tn, LS, 1}, ppy, stw);
         V* Ho = d.spec[pg.out_spec[o]] + F.off_spec + (long long)kz * ny * Kx + kx0;
         for (int idx = threadIdx.x; idx < tn * ny; idx += blockDim.x) {
             int yy = idx / tn, t = idx - yy * tn;
-            Ho[(long long)yy * Kx + t] = r[t * Py + yy];
+            Ho[(long long)yy * Kx + t] = r[t * LS + yy];
         }
         __syncthreads();
+    }
+}
+
+// Register-resident stray-field line pass: one warp per kx line (Py = 32 E, E in {2,4,8,16}).
+// For each input component b: load the x,z spectrum line (y < ny, zero padded), forward FFT in
+// registers, multiply-accumulate with the Newell table in the FFT's own output order; then the
+// adjoint FFT of each output and a store of y < ny.  No block barrier after the twiddle staging.
+template <typename T, int NOUT, int E>
+__device__ __forceinline__ void y_stray_line(const Dev<T>& d, const Film& F, const YProg& pg, int kz, int kx,
+                                             cplx<T>* scr, const cplx<T>* tw, int lane) {
+    using V = cplx<T>;
+    constexpr int P = 32 * E, G = 32 / E;
+    const int ny = F.ny, Kx = F.Kx, Pz = F.Pz;
+    const int Hy = P / 2 + 1, Hz = Pz / 2 + 1;
+    const int kzr = kz <= Pz - kz ? kz : Pz - kz;
+    const bool zodd = kz > Pz / 2;
+    const T* kt = d.ktab + F.off_ktab;
+    const int q = lane / G, g = lane % G;
+    const int s2 = bitrev_lanes(g, G);
+    V acc[NOUT][E];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+        for (int s1 = 0; s1 < E; ++s1) acc[o][s1] = cmk<V>(T(0), T(0));
+    const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx;
+#pragma unroll 1
+    for (int b = 0; b < 3; ++b) {
+        const V* Sb = d.spec[pg.in_spec[b]] + line0;
+        V v[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int y = lane + 32 * k;
+            v[k] = y < ny ? Sb[(long long)y * Kx] : cmk<V>(T(0), T(0));
+        }
+        wreg_fwd<T, E>(v, scr, tw, lane);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            const int cc = pair_idx(pg.slot[o], b);
+            const bool yflip = (cc == 3 || cc == 5);
+            const bool zflip = (cc == 4 || cc == 5) && zodd;
+            const T* kb = kt + (((long long)cc * Hz + kzr) * Kx + kx) * Hy;
+#pragma unroll
+            for (int s1 = 0; s1 < E; ++s1) {
+                const int ky = q + E * (s1 + E * s2);
+                const int kyr = ky <= P / 2 ? ky : P - ky;
+                T k = kb[kyr];
+                if ((yflip && ky > P / 2) != zflip) k = -k;
+                acc[o][s1].x += k * v[s1].x;
+                acc[o][s1].y += k * v[s1].y;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) {
+        wreg_adj<T, E>(acc[o], scr, tw, lane);
+        V* Ho = d.spec[pg.out_spec[o]] + line0;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int y = lane + 32 * k;
+            if (y < ny) Ho[(long long)y * Kx] = acc[o][k];
+        }
+    }
+}
+
+constexpr int kWarpLines = 4;   // kx lines (warps) per CTA of the register stray pass
+
+template <typename T, int NOUT>
+__global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
+    using V = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int4 wi = work[blockIdx.x];
+    const Film& F = d.films[wi.x];
+    const int kz = wi.y, kx0 = wi.z, tn = wi.w;
+    const int Py = F.Py;
+    __shared__ Plan ppy;
+    if (threadIdx.x == 0) ppy = d.plans[F.plan_py];
+    __syncthreads();
+    V* stw = reinterpret_cast<V*>(smem_raw);
+    stage_plan<T>(ppy, d.tw, stw, 0, false);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= tn) return;
+    V* scr = stw + Py + warp * Py;
+    const int kx = kx0 + warp;
+    switch (Py) {
+        case 64: y_stray_line<T, NOUT, 2>(d, F, pg, kz, kx, scr, stw, lane); break;
+        case 128: y_stray_line<T, NOUT, 4>(d, F, pg, kz, kx, scr, stw, lane); break;
+        case 256: y_stray_line<T, NOUT, 8>(d, F, pg, kz, kx, scr, stw, lane); break;
+        default: y_stray_line<T, NOUT, 16>(d, F, pg, kz, kx, scr, stw, lane); break;
     }
 }
 
@@ -387,11 +698,13 @@ __global__ void __launch_bounds__(kThreads) energy_partial_kernel(Dev<T> d, cons
         int y = (loc / nx) % ny;
         int z = loc / sxy;
         long long c = F.off_cell + loc;
-        double v[3] = {(double)m[0][c], (double)m[1][c], (double)m[2][c]};
+        const T* ml[3] = {d.flo[m0], d.flo[m0 + 1], d.flo[m0 + 2]};
+        auto val = [&](int a, long long cc) -> double { return (double)m[a][cc] + (ml[a] ? (double)ml[a][cc] : 0.0); };
+        double v[3] = {val(0, c), val(1, c), val(2, c)};
         for (int a = 0; a < 3; ++a) {
-            if (x + 1 < nx) { double q = (double)m[a][c + 1] - v[a]; ex += q * q / (F.hx * F.hx); }
-            if (y + 1 < ny) { double q = (double)m[a][c + nx] - v[a]; ex += q * q / (F.hy * F.hy); }
-            if (z + 1 < nz) { double q = (double)m[a][c + sxy] - v[a]; ex += q * q / (F.hz * F.hz); }
+            if (x + 1 < nx) { double q = val(a, c + 1) - v[a]; ex += q * q / (F.hx * F.hx); }
+            if (y + 1 < ny) { double q = val(a, c + nx) - v[a]; ex += q * q / (F.hy * F.hy); }
+            if (z + 1 < nz) { double q = val(a, c + sxy) - v[a]; ex += q * q / (F.hz * F.hz); }
         }
         double mu = v[0] * F.u[0] + v[1] * F.u[1] + v[2] * F.u[2];
         an += v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - mu * mu;
@@ -442,7 +755,8 @@ __global__ void energy_final_kernel(const Film* films, int nfilm, const int* __r
 // helpers: dtype conversion in/out of the SoA pools, normalisation, step counter
 // ------------------------------------------------------------------------------------------
 template <typename T, typename S>
-__global__ void copy_in_kernel(T* __restrict__ d0, T* __restrict__ d1, T* __restrict__ d2, const S* __restrict__ src,
+__global__ void copy_in_kernel(T* __restrict__ d0, T* __restrict__ d1, T* __restrict__ d2, T* __restrict__ l0,
+                               T* __restrict__ l1, T* __restrict__ l2, const S* __restrict__ src,
                                const Film* films, int nfilm, long long ntot) {
     // src: concatenation over films of [3][ncell_f]
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -453,13 +767,18 @@ __global__ void copy_in_kernel(T* __restrict__ d0, T* __restrict__ d1, T* __rest
     long long loc = i - F.off_cell;
     long long nc = (long long)F.nx * F.ny * F.nz;
     const S* s = src + 3 * F.off_cell;
-    d0[i] = (T)s[loc];
-    d1[i] = (T)s[nc + loc];
-    d2[i] = (T)s[2 * nc + loc];
+    T* dd[3] = {d0, d1, d2};
+    T* ll[3] = {l0, l1, l2};
+    for (int a = 0; a < 3; ++a) {
+        const double v = (double)s[a * nc + loc];
+        dd[a][i] = (T)v;
+        if (ll[a]) ll[a][i] = (T)(v - (double)(T)v);
+    }
 }
 
 template <typename T, typename S>
 __global__ void copy_out_kernel(S* __restrict__ dst, const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
+                                const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2,
                                 const Film* films, int nfilm, long long ntot) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= ntot) return;
@@ -469,25 +788,30 @@ __global__ void copy_out_kernel(S* __restrict__ dst, const T* __restrict__ d0, c
     long long loc = i - F.off_cell;
     long long nc = (long long)F.nx * F.ny * F.nz;
     S* s = dst + 3 * F.off_cell;
-    s[loc] = (S)d0[i];
-    s[nc + loc] = (S)d1[i];
-    s[2 * nc + loc] = (S)d2[i];
+    const T* dd[3] = {d0, d1, d2};
+    const T* ll[3] = {l0, l1, l2};
+    for (int a = 0; a < 3; ++a) s[a * nc + loc] = (S)((double)dd[a][i] + (ll[a] ? (double)ll[a][i] : 0.0));
 }
 
 template <typename T>
-__global__ void normalize_kernel(T* m0, T* m1, T* m2, long long n, int* status) {
+__global__ void normalize_kernel(T* m0, T* m1, T* m2, T* l0, T* l1, T* l2, long long n, int* status) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    T a = m0[i], b = m1[i], c = m2[i];
-    T n2 = a * a + b * b + c * c;
-    if (!(n2 > T(0)) || !isfinite(n2)) {
+    T* mm[3] = {m0, m1, m2};
+    T* ll[3] = {l0, l1, l2};
+    double v[3];
+    for (int a = 0; a < 3; ++a) v[a] = (double)mm[a][i] + (ll[a] ? (double)ll[a][i] : 0.0);
+    double n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    if (!(n2 > 0.0) || !isfinite(n2)) {
         atomicOr(status, 2);
         return;
     }
-    T inv = T(1) / sqrt(n2);
-    m0[i] = a * inv;
-    m1[i] = b * inv;
-    m2[i] = c * inv;
+    double inv = 1.0 / sqrt(n2);
+    for (int a = 0; a < 3; ++a) {
+        double w = v[a] * inv;
+        mm[a][i] = (T)w;
+        if (ll[a]) ll[a][i] = (T)(w - (double)(T)w);
+    }
 }
 
 template <typename T>

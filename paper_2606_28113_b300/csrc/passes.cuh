@@ -13,32 +13,54 @@ namespace sgspm {
 
 // Shared-memory layout of the XZ pass for one film (host and device agree on it).
 struct XZLayout {
+    int tw;    // complex elements of the staged twiddle tables (x DCT, z DCT, x/z padded FFT)
+    int dt;    // real elements of the staged short-axis DCT tables
     int xw;    // complex elements of each of the two x-work buffers
     int kc;    // kx chunk of the z transforms
     int zw;    // complex elements of each of the two z-work buffers
     int slab;  // real elements of each of the three slabs
 };
 
+// Thin films (nz <= kZReg) transform along z in registers, one thread per column: dense
+// DCT-II / DCT-III (nz x nz tables) and the zero-padded DFT of length Pz <= 2 kZReg.
+constexpr int kZReg = 8;
+
+__host__ __device__ inline bool z_in_registers(int nz) { return nz <= kZReg; }
+
 __host__ __device__ inline XZLayout xz_layout(int nx, int nz, int Px, int Pz, int Kx, bool stray) {
     XZLayout L;
+    const bool zreg = z_in_registers(nz);
     int a = ((nz + 1) / 2) * nx;
-    int b = ((nx + 1) / 2) * nz;
+    int b = zreg ? 0 : ((nx + 1) / 2) * nz;
     int c = stray ? ((nz + 1) / 2) * Px : 0;
     L.xw = a > b ? a : b;
     if (c > L.xw) L.xw = c;
-    L.kc = Kx < 32 ? Kx : 32;
-    L.zw = stray ? Pz * L.kc : 0;
+    L.kc = zreg ? 0 : (Kx < 32 ? Kx : 32);
+    L.zw = (stray && !zreg) ? Pz * L.kc : 0;
     L.slab = nx * nz;
+    L.tw = 2 * nx + 2 * nz + (stray ? Px + Pz : 0);
+    L.dt = zreg ? ((2 * nz * nz + 1) / 2) * 2 : 0;   // even count keeps the complex buffers aligned
     return L;
 }
 
 template <typename T>
 __host__ __device__ inline size_t xz_smem_bytes(const XZLayout& L) {
-    return (size_t)(2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)3 * L.slab * sizeof(T);
+    return (size_t)(L.tw + 2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)(3 * L.slab + L.dt) * sizeof(T);
 }
 
-__host__ __device__ inline int ktab_index(int c, int kx, int kzr, int kyr, int Kx, int Hy, int Hz) {
-    return ((c * Hz + kzr) * Hy + kyr) * Kx + kx;
+// Copy the twiddle tables of `pl` (W_P, and the DCT quarter-wave table when `dct`) from the
+// global pool to shared memory at `stw + off`, and point the plan at the staged copy.
+template <typename T>
+__device__ __forceinline__ void stage_plan(Plan& pl, const cplx<T>* __restrict__ g, cplx<T>* stw, int off, bool dct) {
+    const int P = pl.P;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[off + i] = g[pl.tw + i];
+    if (dct)
+        for (int i = threadIdx.x; i < P; i += blockDim.x) stw[off + P + i] = g[pl.tw4 + i];
+}
+
+// Newell table layout [c][kz'][kx][ky'] (ky' fastest: a y line reads it contiguously)
+__host__ __device__ inline long long ktab_index(int c, int kx, int kzr, int kyr, int Kx, int Hy, int Hz) {
+    return (((long long)c * Hz + kzr) * Kx + kx) * Hy + kyr;
 }
 
 }  // namespace sgspm

@@ -15,12 +15,15 @@ from paper_2606_28113_b300 import inputs, sgspm
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("fp64,rtol", [(True, 1e-12), (False, 1e-12)])
-def test_energy_noalloc_matches_handle_energy_twice(fp64, rtol):
+@pytest.mark.parametrize("fp64", [True, False])
+def test_energy_noalloc_matches_handle_energy_twice(fp64):
+    # The fields are fetched as float64 (exact for both forms: the FP32 form keeps its state
+    # as a double-float pair), so both entry points reduce the same numbers: tolerance 1e-12.
     import torch
     n, h = (40, 24, 4), (1 / 40,) * 3
     kw = dict(eps=0.016, Q=0.03, alpha=0.01, dt=0.01, u=(0.6, 0.8, 0.0), he=(0.02, -0.01, 0.005))
-    tdt = torch.float64 if fp64 else torch.float32
+    tdt = torch.float64
+    rtol = 1e-12
     H = sgspm.film(n, h, fp64=fp64, **kw)
     for seed in (0, 1):                       # two calls in a row, on different states
         H.set_m(inputs.random_unit(seed, n))
@@ -35,6 +38,11 @@ def test_energy_noalloc_matches_handle_energy_twice(fp64, rtol):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.all(np.abs(got - ref) <= rtol * np.abs(ref).max()), (got, ref)
+        # the float32 input path, against the same reference within the FP32 tolerance
+        out32 = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+        sgspm.energy_noalloc(n, h, kw["eps"], kw["Q"], kw["u"], kw["he"], m.float(), hs.float(), out32)
+        torch.cuda.synchronize()
+        assert np.all(np.abs(out32.cpu().numpy() - ref) <= 1e-5 * np.abs(ref).max())
     H.close()
 
 
