@@ -176,22 +176,44 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
             const T hea = T(F.he[a]);
             const long long sz = (long long)nx * ny;
-            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                const int z = idx / nx, x = idx - z * nx;
-                const long long c = cell_of(z, x);
-                const T v1 = m1[c], v2 = m2[c], v3 = m3[c];
-                const T mc = ma[c];
-                const T mcl = ml ? ml[c] : T(0);
-                const T mu = v1 * ux + v2 * uy + v3 * uz;
-                // mirror ghosts: a missing neighbour contributes a zero difference
-                auto dif = [&](long long o) -> T { return (ma[c + o] - mc) + (ml ? ml[c + o] - mcl : T(0)); };
-                T lap = T(0);
-                if (nx > 1) lap += ihx * ((x + 1 < nx ? dif(1) : T(0)) + (x > 0 ? dif(-1) : T(0)));
-                if (ny > 1) lap += ihy * ((y + 1 < ny ? dif(nx) : T(0)) + (y > 0 ? dif(-nx) : T(0)));
-                if (nz > 1) lap += ihz * ((z + 1 < nz ? dif(sz) : T(0)) + (z > 0 ? dif(-sz) : T(0)));
-                const T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
-                const T f = -Q * (mc - mu * ua) + h[idx] + he;
-                h[idx] = scale * (f + eps * lap);
+            // batches of kB cells per thread: every load of the batch is issued before any use
+            constexpr int kB = sizeof(T) == 4 ? 4 : 2;
+            for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
+                T v1[kB], v2[kB], v3[kB], mc[kB], mcl[kB], nb[kB][6], nl[kB][6];
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int idx = i0 + u * blockDim.x;
+                    if (idx >= nxz) break;
+                    const int z = idx / nx, x = idx - z * nx;
+                    const long long c = cell_of(z, x);
+                    v1[u] = m1[c];
+                    v2[u] = m2[c];
+                    v3[u] = m3[c];
+                    mc[u] = ma[c];
+                    mcl[u] = ml ? ml[c] : T(0);
+                    // neighbours with mirror ghosts (a missing neighbour repeats the cell)
+                    const long long o[6] = {x + 1 < nx ? 1 : 0, x > 0 ? -1 : 0, y + 1 < ny ? (long long)nx : 0,
+                                            y > 0 ? -(long long)nx : 0, z + 1 < nz ? sz : 0, z > 0 ? -sz : 0};
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        nb[u][k] = ma[c + o[k]];
+                        nl[u][k] = ml ? ml[c + o[k]] : T(0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int idx = i0 + u * blockDim.x;
+                    if (idx >= nxz) break;
+                    const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
+                    const T mu = v1[u] * ux + v2[u] * uy + v3[u] * uz;
+                    T d6[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) d6[k] = (nb[u][k] - mc[u]) + (nl[u][k] - mcl[u]);
+                    const T lap = ihx * (d6[0] + d6[1]) + ihy * (d6[2] + d6[3]) + ihz * (d6[4] + d6[5]);
+                    const T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
+                    const T f = -Q * (mc[u] - mu * ua) + h[idx] + he;
+                    h[idx] = scale * (f + eps * lap);
+                }
             }
         }
         __syncthreads();
@@ -272,30 +294,44 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         const T* bl_ = pg.gs_base >= 0 ? d.flo[pg.gs_base] : nullptr;
         const T* ql_ = pg.gs_q >= 0 ? d.flo[pg.gs_q] : nullptr;
         const T* sl_ = pg.gs_s >= 0 ? d.flo[pg.gs_s] : nullptr;
-        for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-            int z = idx / nx, x = idx - z * nx;
-            long long c = cell_of(z, x);
-            T b = load_ref(d, pg.gs_base, c, slabs, S, idx);
-            T p = load_ref(d, pg.gs_p, c, slabs, S, idx);
-            T q = load_ref(d, pg.gs_q, c, slabs, S, idx);
-            T r = load_ref(d, pg.gs_r, c, slabs, S, idx);
-            T s = load_ref(d, pg.gs_s, c, slabs, S, idx);
-            if (outl) {
-                // double-float state: base (hi, lo) + increment p (q_hi + q_lo) - r (s_hi + s_lo)
-                const T ql = ql_ ? ql_[c] : T(0), sl = sl_ ? sl_[c] : T(0), bl = bl_ ? bl_[c] : T(0);
-                const T rs = fma(r, sl, r * s);
-                const T inc = fma(p, q, fma(p, ql, -rs));
-                T hi, e;
-                two_sum(b, inc, hi, e);
-                T h2, l2;
-                fast_two_sum(hi, e + bl, h2, l2);
-                out[c] = h2;
-                outl[c] = l2;
-                res[idx] = h2;
-            } else {
-                T v = b + (p * q - r * s);
-                out[c] = v;
-                res[idx] = v;
+        constexpr int kB = sizeof(T) == 4 ? 4 : 2;
+        for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
+            T bb[kB], pp[kB], qq[kB], rr[kB], ss[kB], bl[kB], ql[kB], sl[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int idx = i0 + u * blockDim.x;
+                if (idx >= nxz) break;
+                const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
+                bb[u] = load_ref(d, pg.gs_base, c, slabs, S, idx);
+                pp[u] = load_ref(d, pg.gs_p, c, slabs, S, idx);
+                qq[u] = load_ref(d, pg.gs_q, c, slabs, S, idx);
+                rr[u] = load_ref(d, pg.gs_r, c, slabs, S, idx);
+                ss[u] = load_ref(d, pg.gs_s, c, slabs, S, idx);
+                bl[u] = bl_ ? bl_[c] : T(0);
+                ql[u] = ql_ ? ql_[c] : T(0);
+                sl[u] = sl_ ? sl_[c] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int idx = i0 + u * blockDim.x;
+                if (idx >= nxz) break;
+                const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
+                if (outl) {
+                    // double-float state: base (hi, lo) + increment p (q_hi + q_lo) - r (s_hi + s_lo)
+                    const T rs = fma(rr[u], sl[u], rr[u] * ss[u]);
+                    const T inc = fma(pp[u], qq[u], fma(pp[u], ql[u], -rs));
+                    T hi, e;
+                    two_sum(bb[u], inc, hi, e);
+                    T h2, l2;
+                    fast_two_sum(hi, e + bl[u], h2, l2);
+                    out[c] = h2;
+                    outl[c] = l2;
+                    res[idx] = h2;
+                } else {
+                    const T v = bb[u] + (pp[u] * qq[u] - rr[u] * ss[u]);
+                    out[c] = v;
+                    res[idx] = v;
+                }
             }
         }
         __syncthreads();
