@@ -134,6 +134,24 @@ int sgspm_set_forcing(sgspm_t h, int kind);
 int sgspm_set_time(sgspm_t h, double t);
 int sgspm_get_time(sgspm_t h, double* t);
 
+/*
+ * Adjoint (reverse mode) of the SGSPM step, for gradients of a loss L(m(T)) with respect to the
+ * per-cell applied field h_e and the damping alpha.  SGSPM with f refreshed at every state
+ * (no SGSPM_GSPM, no SGSPM_FROZEN_STRAY), no manufactured forcing.
+ *
+ * sgspm_record: from the current m (= m(0)), advance nsteps >= 1 steps, keeping a checkpoint of
+ *   the state every K >= 1 steps in device memory (nsteps/K checkpoints).  Afterwards m = m(T).
+ * sgspm_grad: dL_dmT = dL/dm(T) in the field layout (host or device, dtype SGSPM_F32 or
+ *   SGSPM_F64_DATA).  Runs the reverse sweep: each segment is recomputed from its checkpoint and
+ *   every step is replayed once more in recording form (storing its intermediates) before the
+ *   hand-written reverse of that step.  Writes dL/dh_e (same layout and dtype as dL_dmT; the
+ *   gradient with respect to a per-cell applied field, also when the field is uniform) and
+ *   dL/dalpha (nfilm host doubles).  Only the dependence through m(T) is included: a loss term
+ *   on h_e or alpha itself is the caller's.  Synchronises; m is m(T) again on return.
+ */
+int sgspm_record(sgspm_t h, long long nsteps, int K);
+int sgspm_grad(sgspm_t h, const void* dL_dmT, int dtype, void* dL_dhe, double* dL_dalpha);
+
 /* Wait for all enqueued work and report the latched device status. */
 int sgspm_sync(sgspm_t h);
 

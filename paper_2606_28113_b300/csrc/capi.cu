@@ -13,18 +13,31 @@
 #include "passes.cu"
 #include "newell.cu"
 #include "noalloc.cu"
+#include "adjoint.cu"
 
 namespace sgspm {
 
-// real field slots
-enum { M1 = 0, M2, M3, A1, A2, A3, B1, B2, E3N, E1S, E3SS, D1, D2, D3, HS1, HS2, HS3, NSLOT };
+// real field slots: the forward step's, then (allocated by sgspm_record) the recorded
+// intermediates of a step and the adjoint accumulators
+enum {
+    M1 = 0, M2, M3, A1, A2, A3, B1, B2, E3N, E1S, E3SS, D1, D2, D3, HS1, HS2, HS3, NSLOT_FWD,
+    D2N = NSLOT_FWD, D2S, D2SS, V1, V2, V3, MN1, MN2, MN3, ERS1, ERS2, ERS3,
+    G1, G2, G3, bM1, bM2, bM3, bA1, bA2, bA3, bB1, bB2, bD2N, bE3N, bE1S, bD2S, bE3SS, bD2SS,
+    RB1, RB2, RB3, FB1, FB2, FB3, HF1, HF2, HF3, bHE1, bHE2, bHE3, NSLOT
+};
+static_assert(NSLOT <= kMaxSlots, "slot table too small");
 // spectral slots
-enum { S1 = 0, S2, S3, H1, H2, H3, NSPEC };
+enum { S1 = 0, S2, S3, H1, H2, H3, NSPEC_FWD, SA1 = NSPEC_FWD, SA2, SA3, NSPEC };
 
 struct Launch {
-    int kind;   // 0 xz, 1 y heat, 2 y stray, 3 step counter
+    int kind;   // 0 xz, 1 y heat, 2 y stray, 3 step counter, 4 adj GS, 5 adj f, 6 adj ew, 7 adj proj, 8 adj alpha
     XZProg xz;
     YProg y;
+    AdjGS gs;
+    AdjF af;
+    AdjEw ew;
+    AdjProj pj;
+    AdjAlpha al;
 };
 
 }  // namespace sgspm
@@ -50,9 +63,22 @@ struct sgspm_ctx {
     void* d_lam = nullptr;
     void* d_dtab = nullptr;
     void* d_ktab = nullptr;
-    void* d_field[NSLOT] = {};
-    void* d_flo[NSLOT] = {};           // low parts of the double-float state slots (FP32 form)
-    void* d_spec[NSPEC] = {};
+    void* d_field[kMaxSlots] = {};
+    void* d_flo[kMaxSlots] = {};       // low parts of the double-float state slots (FP32 form)
+    void* d_spec[kMaxSpec] = {};
+    void** d_tab = nullptr;            // device copies of the three pointer tables
+    void** d_tab_lo = nullptr;
+    void** d_tab_spec = nullptr;
+    // recorded forward (adjoint)
+    bool rec_alloc = false;
+    long long rec_nsteps = 0;
+    int rec_K = 0;
+    void* d_ckpt = nullptr;            // checkpoints: [seg][hi/lo][3][ncell]
+    void* d_seg = nullptr;             // states of one segment: [K][hi/lo][3][ncell]
+    void* d_final = nullptr;           // m(T) while the reverse sweep runs
+    double* d_apart = nullptr;         // alpha gradient block partials
+    double* d_alpha_b = nullptr;       // alpha gradient per film
+    std::vector<Launch> rec_prog, adj_prog;
     void* d_he = nullptr;
     bool he_cell = false;
     int* d_status = nullptr;
@@ -156,9 +182,9 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
     d.lam = (const T*)ctx->d_lam;
     d.dtab = (const T*)ctx->d_dtab;
     d.ktab = (const T*)ctx->d_ktab;
-    for (int i = 0; i < kMaxSlots; ++i) d.field[i] = i < NSLOT ? (T*)ctx->d_field[i] : nullptr;
-    for (int i = 0; i < kMaxSlots; ++i) d.flo[i] = i < NSLOT ? (T*)ctx->d_flo[i] : nullptr;
-    for (int i = 0; i < kMaxSpec; ++i) d.spec[i] = i < NSPEC ? (cplx<T>*)ctx->d_spec[i] : nullptr;
+    d.field = (T* const*)ctx->d_tab;
+    d.flo = (T* const*)ctx->d_tab_lo;
+    d.spec = (cplx<T>* const*)ctx->d_tab_spec;
     d.he_cell = ctx->he_cell ? (const T*)ctx->d_he : nullptr;
     d.status = ctx->d_status;
     d.step_ctr = ctx->d_step;
@@ -187,8 +213,25 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
             }
             break;
         }
-        default:
+        case 3:
             step_counter_kernel<<<1, 1, 0, st>>>(ctx->d_step);
+            break;
+        case 4:
+            adj_gs_kernel<T><<<ctx->n_e, kThreads, 0, st>>>(d, ctx->d_work_e, L.gs);
+            break;
+        case 5:
+            adj_f_kernel<T><<<ctx->n_e, kThreads, 0, st>>>(d, ctx->d_work_e, L.af);
+            break;
+        case 6:
+            adj_ew_kernel<T><<<ctx->n_e, kThreads, 0, st>>>(d, ctx->d_work_e, L.ew);
+            break;
+        case 7:
+            adj_proj_kernel<T><<<ctx->n_e, kThreads, 0, st>>>(d, ctx->d_work_e, L.pj);
+            break;
+        default:
+            adj_alpha_partial_kernel<T><<<ctx->n_e, kThreads, 0, st>>>(d, ctx->d_work_e, L.al, ctx->d_apart);
+            adj_alpha_final_kernel<<<(ctx->nfilm + 127) / 128, 128, 0, st>>>(ctx->nfilm, ctx->d_first_e, ctx->d_apart,
+                                                                              ctx->d_alpha_b);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -215,6 +258,8 @@ static XZProg xz_empty() {
         p.rhs_h[i] = -1;
         p.rhs_hs_store[i] = -1;
         p.inv_store[i] = -1;
+        p.rhs_copy[i] = -1;
+        p.fin_v[i] = -1;
     }
     p.rhs_dct = 1;
     return p;
@@ -226,6 +271,7 @@ static Launch mk_ystray(const std::vector<int>& outs) {
     L.kind = 2;
     L.y.kind = 1;
     L.y.n = (int)outs.size();
+    L.y.in_mask = 7;
     for (int i = 0; i < 3; ++i) L.y.in_spec[i] = S1 + i;
     for (size_t o = 0; o < outs.size(); ++o) {
         L.y.slot[o] = outs[o];
@@ -312,6 +358,221 @@ static Launch mk_final(const sgspm_ctx* ctx, int i0, int i1, int i2) {
         }
     }
     return L;
+}
+
+// One SGSPM step (R1) that also stores every intermediate the reverse step needs: all six
+// deltas, h_s(m**), m*** and the new state in MN1..3 (M1..3 keep m^n).
+static void build_record(sgspm_ctx* ctx) {
+    const bool st = ctx->stray;
+    std::vector<Launch>& P = ctx->rec_prog;
+    P.clear();
+    if (st) P.push_back(mk_ystray({1, 2}));
+    P.push_back(mk_rhs(ctx, {1, 2}, M1, M2, M3, 0));
+    P.push_back(mk_yheat({1, 2}, 0));
+    {
+        Launch L = mk_gs(ctx, 1, -1, A1, M1, slab(0), M3, slab(1), M2, 0);
+        L.xz.n_inv = 2;
+        L.xz.inv_in[0] = D2;
+        L.xz.inv_in[1] = D3;
+        L.xz.inv_store[0] = D2N;
+        L.xz.inv_store[1] = E3N;
+        P.push_back(L);
+    }
+    if (st) P.push_back(mk_ystray({0}));
+    P.push_back(mk_rhs(ctx, {0}, A1, M2, M3, 0));
+    P.push_back(mk_yheat({0}, 0));
+    P.push_back(mk_gs(ctx, 0, E1S, A2, M2, E3N, A1, slab(0), M3, 1));
+    if (st) P.push_back(mk_ystray({1}));
+    P.push_back(mk_rhs(ctx, {1}, A1, A2, M3, 0));
+    P.push_back(mk_yheat({1}, 0));
+    P.push_back(mk_gs(ctx, 1, D2S, A3, M3, E1S, A2, slab(0), A1, 2));
+    if (st) P.push_back(mk_ystray({2}));
+    P.push_back(mk_rhs(ctx, {2}, A1, A2, A3, 0));
+    P.push_back(mk_yheat({2}, 0));
+    P.push_back(mk_gs(ctx, 2, E3SS, B2, M2, slab(0), A1, E1S, A3, 1));
+    if (st) P.push_back(mk_ystray({1}));
+    P.push_back(mk_rhs(ctx, {1}, A1, B2, A3, 0));
+    P.push_back(mk_yheat({1}, 0));
+    P.push_back(mk_gs(ctx, 1, D2SS, B1, M1, slab(0), A3, E3SS, B2, 0));
+    if (st) P.push_back(mk_ystray({0, 1, 2}));
+    {
+        Launch L = mk_rhs(ctx, {0, 1, 2}, B1, B2, A3, 1);
+        if (st)
+            for (int i = 0; i < 3; ++i) L.xz.rhs_hs_store[i] = ERS1 + i;
+        P.push_back(L);
+    }
+    P.push_back(mk_yheat({0, 1, 2}, 1));
+    {
+        Launch L = mk_final(ctx, B1, B2, A3);
+        for (int i = 0; i < 3; ++i) {
+            L.xz.fin_out[i] = MN1 + i;
+            L.xz.fin_v[i] = V1 + i;
+        }
+        L.xz.n_fwd = 0;
+        P.push_back(L);
+    }
+}
+
+// The reverse of one recorded step: G1..3 holds dL/dm^{n+1} on entry and dL/dm^n on exit;
+// dL/dh_e accumulates in bHE1..3 and dL/dalpha per film in d_alpha_b.
+static void build_adjoint(sgspm_ctx* ctx) {
+    const bool st = ctx->stray;
+    std::vector<Launch>& P = ctx->adj_prog;
+    P.clear();
+    auto blank = [](int kind) {
+        Launch L;
+        memset(&L, 0, sizeof(L));
+        L.kind = kind;
+        L.xz = xz_empty();
+        return L;
+    };
+    auto ew = [&](int mode, const std::vector<int>& dst, const std::vector<int>& src) {
+        for (size_t i0 = 0; i0 < dst.size(); i0 += 12) {
+            Launch L = blank(6);
+            L.ew.mode = mode;
+            L.ew.n = (int)std::min<size_t>(12, dst.size() - i0);
+            for (int k = 0; k < L.ew.n; ++k) {
+                L.ew.dst[k] = dst[i0 + k];
+                L.ew.src[k] = src.empty() ? 0 : src[i0 + k];
+            }
+            P.push_back(L);
+        }
+    };
+    auto solve = [&](const std::vector<int>& src, const std::vector<int>& dst, int damp) {
+        const int k = (int)src.size();
+        Launch X = blank(0);
+        X.xz.n_rhs = k;
+        for (int i = 0; i < k; ++i) {
+            X.xz.rhs_comp[i] = i;
+            X.xz.rhs_copy[i] = src[i];
+            X.xz.rhs_out[i] = D1 + i;
+        }
+        X.xz.state[0] = M1;
+        X.xz.state[1] = M2;
+        X.xz.state[2] = M3;
+        P.push_back(X);
+        std::vector<int> comps;
+        for (int i = 0; i < k; ++i) comps.push_back(i);
+        P.push_back(mk_yheat(comps, damp));
+        Launch I = blank(0);
+        I.xz.n_inv = k;
+        for (int i = 0; i < k; ++i) {
+            I.xz.inv_in[i] = D1 + i;
+            I.xz.inv_store[i] = dst[i];
+        }
+        P.push_back(I);
+    };
+    auto fadj = [&](const std::vector<int>& comps, const std::vector<int>& rho, const std::vector<int>& fb,
+                    const int sb[3], int damp) {
+        Launch L = blank(5);
+        L.af.n = (int)comps.size();
+        for (int k = 0; k < L.af.n; ++k) {
+            L.af.comp[k] = comps[k];
+            L.af.rho[k] = rho[k];
+            L.af.fb[k] = fb[k];
+        }
+        for (int k = 0; k < 3; ++k) L.af.sb[k] = sb[k];
+        L.af.heb = bHE1;
+        L.af.damp = damp;
+        P.push_back(L);
+    };
+    auto stray = [&](const std::vector<int>& comps, const std::vector<int>& fb, const int sb[3]) {
+        if (!st) return;
+        Launch F = blank(0);
+        F.xz.n_fwd = (int)comps.size();
+        int mask = 0;
+        for (size_t k = 0; k < comps.size(); ++k) {
+            F.xz.fwd_src[k] = fb[k];
+            F.xz.fwd_dst[k] = SA1 + comps[k];
+            mask |= 1 << comps[k];
+        }
+        P.push_back(F);
+        Launch Y = mk_ystray({0, 1, 2});
+        Y.y.in_mask = mask;
+        for (int i = 0; i < 3; ++i) Y.y.in_spec[i] = SA1 + i;
+        P.push_back(Y);
+        Launch Hs = blank(0);
+        Hs.xz.n_rhs = 3;
+        Hs.xz.rhs_dct = 0;
+        for (int i = 0; i < 3; ++i) {
+            Hs.xz.rhs_comp[i] = i;
+            Hs.xz.rhs_h[i] = H1 + i;
+            Hs.xz.rhs_hs_store[i] = HF1 + i;
+        }
+        Hs.xz.state[0] = M1;
+        Hs.xz.state[1] = M2;
+        Hs.xz.state[2] = M3;
+        P.push_back(Hs);
+        ew(0, {sb[0], sb[1], sb[2]}, {HF1, HF2, HF3});
+    };
+    auto gs = [&](int ub, int base_b, int p, int p_b, int q, int q_b, int r, int r_b, int s_, int s_b) {
+        Launch L = blank(4);
+        L.gs = AdjGS{ub, base_b, p, p_b, q, q_b, r, r_b, s_, s_b};
+        P.push_back(L);
+    };
+    ew(1, {bM1, bM2, bM3, bA1, bA2, bA3, bB1, bB2, bD2N, bE3N, bE1S, bD2S, bE3SS, bD2SS}, {});
+    // projection and damping heat flow (Steps 3 and 2)
+    {
+        Launch L = blank(7);
+        for (int k = 0; k < 3; ++k) {
+            L.pj.g[k] = G1 + k;
+            L.pj.mn[k] = MN1 + k;
+            L.pj.v[k] = V1 + k;
+            L.pj.vb[k] = RB1 + k;
+        }
+        L.pj.eb[0] = bB1;
+        L.pj.eb[1] = bB2;
+        L.pj.eb[2] = bA3;
+        P.push_back(L);
+    }
+    solve({RB1, RB2, RB3}, {RB1, RB2, RB3}, 1);
+    {
+        Launch L = blank(8);
+        for (int k = 0; k < 3; ++k) {
+            L.al.rho[k] = RB1 + k;
+            L.al.hs[k] = ERS1 + k;
+            L.al.v[k] = V1 + k;
+        }
+        L.al.e[0] = B1;
+        L.al.e[1] = B2;
+        L.al.e[2] = A3;
+        L.al.have_hs = st ? 1 : 0;
+        P.push_back(L);
+    }
+    const int sE[3] = {bB1, bB2, bA3};
+    fadj({0, 1, 2}, {RB1, RB2, RB3}, {FB1, FB2, FB3}, sE, 1);
+    stray({0, 1, 2}, {FB1, FB2, FB3}, sE);
+    // m1** = m1 + d2** m3** - d3** m2**;  d2** at D = (m1*, m2**, m3**)
+    gs(bB1, bM1, D2SS, bD2SS, A3, bA3, E3SS, bE3SS, B2, bB2);
+    const int sD[3] = {bA1, bB2, bA3};
+    solve({bD2SS}, {RB2}, 0);
+    fadj({1}, {RB2}, {FB2}, sD, 0);
+    stray({1}, {FB2}, sD);
+    // m2** = m2 + d3** m1* - d1* m3**;  d3** at C = (m1*, m2*, m3*)
+    gs(bB2, bM2, E3SS, bE3SS, A1, bA1, E1S, bE1S, A3, bA3);
+    const int sC[3] = {bA1, bA2, bA3};
+    solve({bE3SS}, {RB3}, 0);
+    fadj({2}, {RB3}, {FB3}, sC, 0);
+    stray({2}, {FB3}, sC);
+    // m3* = m3 + d1* m2* - d2* m1*;  d2* at B = (m1*, m2*, m3)
+    gs(bA3, bM3, E1S, bE1S, A2, bA2, D2S, bD2S, A1, bA1);
+    const int sB[3] = {bA1, bA2, bM3};
+    solve({bD2S}, {RB2}, 0);
+    fadj({1}, {RB2}, {FB2}, sB, 0);
+    stray({1}, {FB2}, sB);
+    // m2* = m2 + d3n m1* - d1* m3;  d1* at A = (m1*, m2, m3)
+    gs(bA2, bM2, E3N, bE3N, A1, bA1, E1S, bE1S, M3, bM3);
+    const int sA[3] = {bA1, bM2, bM3};
+    solve({bE1S}, {RB1}, 0);
+    fadj({0}, {RB1}, {FB1}, sA, 0);
+    stray({0}, {FB1}, sA);
+    // m1* = m1 + d2n m3 - d3n m2;  d2n, d3n at m^n
+    gs(bA1, bM1, D2N, bD2N, M3, bM3, E3N, bE3N, M2, bM2);
+    const int sM[3] = {bM1, bM2, bM3};
+    solve({bD2N, bE3N}, {RB2, RB3}, 0);
+    fadj({1, 2}, {RB2, RB3}, {FB2, FB3}, sM, 0);
+    stray({1, 2}, {FB2, FB3}, sM);
+    ew(2, {G1, G2, G3}, {bM1, bM2, bM3});
 }
 
 static void build_programs(sgspm_ctx* ctx) {
@@ -435,6 +696,18 @@ static void build_programs(sgspm_ctx* ctx) {
         }
         ctx->fwd_prog.push_back(L);
     }
+}
+
+static int upload_tables(sgspm_ctx* ctx) {
+    if (!ctx->d_tab) {
+        CK(cudaMalloc(&ctx->d_tab, kMaxSlots * sizeof(void*)));
+        CK(cudaMalloc(&ctx->d_tab_lo, kMaxSlots * sizeof(void*)));
+        CK(cudaMalloc(&ctx->d_tab_spec, kMaxSpec * sizeof(void*)));
+    }
+    CK(cudaMemcpy(ctx->d_tab, ctx->d_field, kMaxSlots * sizeof(void*), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tab_lo, ctx->d_flo, kMaxSlots * sizeof(void*), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tab_spec, ctx->d_spec, kMaxSpec * sizeof(void*), cudaMemcpyHostToDevice));
+    return SGSPM_OK;
 }
 
 static int drop_graph(sgspm_ctx* ctx) {
@@ -757,7 +1030,7 @@ static int setup_t(sgspm_ctx* ctx) {
     CK(cudaMalloc(&ctx->d_plans, ctx->plans.size() * sizeof(Plan)));
     CK(cudaMemcpy(ctx->d_plans, ctx->plans.data(), ctx->plans.size() * sizeof(Plan), cudaMemcpyHostToDevice));
     // pools
-    for (int i = 0; i < NSLOT; ++i) {
+    for (int i = 0; i < NSLOT_FWD; ++i) {
         CK(cudaMalloc(&ctx->d_field[i], (size_t)ctx->ncell * sizeof(T)));
         CK(cudaMemset(ctx->d_field[i], 0, (size_t)ctx->ncell * sizeof(T)));
     }
@@ -770,7 +1043,7 @@ static int setup_t(sgspm_ctx* ctx) {
         }
     }
     if (ctx->stray) {
-        for (int i = 0; i < NSPEC; ++i) {
+        for (int i = 0; i < NSPEC_FWD; ++i) {
             CK(cudaMalloc(&ctx->d_spec[i], (size_t)ctx->nspec * V));
             CK(cudaMemset(ctx->d_spec[i], 0, (size_t)ctx->nspec * V));
         }
@@ -785,6 +1058,7 @@ static int setup_t(sgspm_ctx* ctx) {
     CK(cudaMemset(ctx->d_step, 0, sizeof(long long)));
     CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
     ctx->tsz = sizeof(T);
+    if ((rc = upload_tables(ctx))) return rc;
     build_programs(ctx);
     CK(cudaDeviceSynchronize());
     return SGSPM_OK;
@@ -797,12 +1071,16 @@ static void release(sgspm_ctx* ctx) {
                     ctx->d_work_yw};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    for (int i = 0; i < NSLOT; ++i) {
+    for (int i = 0; i < kMaxSlots; ++i) {
         if (ctx->d_field[i]) cudaFree(ctx->d_field[i]);
         if (ctx->d_flo[i]) cudaFree(ctx->d_flo[i]);
     }
-    for (int i = 0; i < NSPEC; ++i)
+    for (int i = 0; i < kMaxSpec; ++i)
         if (ctx->d_spec[i]) cudaFree(ctx->d_spec[i]);
+    void* more[] = {ctx->d_tab, ctx->d_tab_lo, ctx->d_tab_spec, ctx->d_ckpt, ctx->d_seg, ctx->d_final, ctx->d_apart,
+                    ctx->d_alpha_b};
+    for (void* p : more)
+        if (p) cudaFree(p);
     for (int n = 0; n < 4; ++n)
         if (ctx->d_work_ys[n]) cudaFree(ctx->d_work_ys[n]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -898,6 +1176,139 @@ static int get_field_t(sgspm_t ctx, int which, void* ptr, int dtype) {
     CK(cudaGetLastError());
     const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
     CK(cudaMemcpyAsync(ptr, ctx->d_stage, bytes, cudaMemcpyDefault, ctx->stream));
+    return check_status(ctx);
+}
+
+// Allocate the slots, spectra and buffers a recorded forward and its reverse need.
+template <typename T>
+static int rec_alloc_t(sgspm_ctx* ctx, long long nseg, int K) {
+    const size_t cell = (size_t)ctx->ncell * sizeof(T);
+    if (!ctx->rec_alloc) {
+        for (int i = NSLOT_FWD; i < NSLOT; ++i) {
+            CK(cudaMalloc(&ctx->d_field[i], cell));
+            CK(cudaMemset(ctx->d_field[i], 0, cell));
+        }
+        if (sizeof(T) == 4)
+            for (int i = MN1; i <= MN3; ++i) {
+                CK(cudaMalloc(&ctx->d_flo[i], cell));
+                CK(cudaMemset(ctx->d_flo[i], 0, cell));
+            }
+        if (ctx->stray)
+            for (int i = NSPEC_FWD; i < NSPEC; ++i) {
+                CK(cudaMalloc(&ctx->d_spec[i], (size_t)ctx->nspec * sizeof(cplx<T>)));
+                CK(cudaMemset(ctx->d_spec[i], 0, (size_t)ctx->nspec * sizeof(cplx<T>)));
+            }
+        CK(cudaMalloc(&ctx->d_apart, std::max(1, ctx->n_e) * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_alpha_b, ctx->nfilm * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_final, 6 * cell));
+        ctx->rec_alloc = true;
+        int rc = upload_tables(ctx);
+        if (rc) return rc;
+        build_record(ctx);
+        build_adjoint(ctx);
+    }
+    if (ctx->d_ckpt) cudaFree(ctx->d_ckpt);
+    if (ctx->d_seg) cudaFree(ctx->d_seg);
+    ctx->d_ckpt = ctx->d_seg = nullptr;
+    CK(cudaMalloc(&ctx->d_ckpt, (size_t)nseg * 6 * cell));
+    CK(cudaMalloc(&ctx->d_seg, (size_t)K * 6 * cell));
+    return SGSPM_OK;
+}
+
+// state (M1..3 hi/lo) <-> buf [hi 3][lo 3] of ncell each
+template <typename T>
+static int state_io(sgspm_ctx* ctx, T* buf, bool save) {
+    const long long n = ctx->ncell;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    for (int a = 0; a < 3; ++a) {
+        T* hi = buf + a * n;
+        T* lo = buf + (3 + a) * n;
+        T* mh = (T*)ctx->d_field[M1 + a];
+        T* ml = (T*)ctx->d_flo[M1 + a];
+        if (save) state_copy_kernel<T><<<nb, 256, 0, ctx->stream>>>(hi, lo, mh, ml, n);
+        else state_copy_kernel<T><<<nb, 256, 0, ctx->stream>>>(mh, ml, hi, ml ? lo : nullptr, n);
+    }
+    CK(cudaGetLastError());
+    return SGSPM_OK;
+}
+
+template <typename T>
+static int record_t(sgspm_ctx* ctx, long long nsteps, int K) {
+    const long long nseg = (nsteps + K - 1) / K;
+    int rc = rec_alloc_t<T>(ctx, nseg, K);
+    if (rc) return rc;
+    T* ck = (T*)ctx->d_ckpt;
+    const long long per = 6 * ctx->ncell;
+    for (long long sgi = 0; sgi < nseg; ++sgi) {
+        if ((rc = state_io<T>(ctx, ck + sgi * per, true))) return rc;
+        const long long n = std::min<long long>(K, nsteps - sgi * K);
+        if ((rc = sgspm_step(ctx, n))) return rc;
+    }
+    ctx->rec_nsteps = nsteps;
+    ctx->rec_K = K;
+    return check_status(ctx);
+}
+
+template <typename T>
+static int grad_t(sgspm_ctx* ctx, const void* dL_dmT, int dtype, void* dL_dhe, double* dL_dalpha) {
+    const long long n = ctx->ncell;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const long long nsteps = ctx->rec_nsteps;
+    const int K = ctx->rec_K;
+    const long long nseg = (nsteps + K - 1) / K;
+    const long long per = 6 * n;
+    int rc;
+    // dL/dm(T) -> G1..3 ; m(T) saved for the end
+    const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
+    CK(cudaMemcpyAsync(ctx->d_stage, dL_dmT, bytes, cudaMemcpyDefault, ctx->stream));
+    T* g0 = (T*)ctx->d_field[G1];
+    T* g1 = (T*)ctx->d_field[G2];
+    T* g2 = (T*)ctx->d_field[G3];
+    if (dtype == SGSPM_F64_DATA)
+        copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(g0, g1, g2, nullptr, nullptr, nullptr,
+                                                               (const double*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+    else
+        copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(g0, g1, g2, nullptr, nullptr, nullptr,
+                                                              (const float*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+    CK(cudaGetLastError());
+    if ((rc = state_io<T>(ctx, (T*)ctx->d_final, true))) return rc;
+    for (int a = 0; a < 3; ++a) CK(cudaMemsetAsync(ctx->d_field[bHE1 + a], 0, (size_t)n * sizeof(T), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_alpha_b, 0, ctx->nfilm * sizeof(double), ctx->stream));
+    T* ck = (T*)ctx->d_ckpt;
+    T* sg = (T*)ctx->d_seg;
+    for (long long sgi = nseg - 1; sgi >= 0; --sgi) {
+        const long long L = std::min<long long>(K, nsteps - sgi * K);
+        // recompute the segment's step states
+        if ((rc = state_io<T>(ctx, ck + sgi * per, false))) return rc;
+        if ((rc = run_prog(ctx, ctx->fwd_prog, ctx->stream))) return rc;
+        for (long long j = 0; j < L; ++j) {
+            if ((rc = state_io<T>(ctx, sg + j * per, true))) return rc;
+            if (j + 1 < L && (rc = run_prog(ctx, ctx->step_prog, ctx->stream))) return rc;
+        }
+        // reverse through the segment
+        for (long long j = L - 1; j >= 0; --j) {
+            if ((rc = state_io<T>(ctx, sg + j * per, false))) return rc;
+            if ((rc = run_prog(ctx, ctx->fwd_prog, ctx->stream))) return rc;
+            if ((rc = run_prog(ctx, ctx->rec_prog, ctx->stream))) return rc;
+            if ((rc = run_prog(ctx, ctx->adj_prog, ctx->stream))) return rc;
+        }
+    }
+    // outputs
+    const T* h0 = (const T*)ctx->d_field[bHE1];
+    const T* h1 = (const T*)ctx->d_field[bHE2];
+    const T* h2 = (const T*)ctx->d_field[bHE3];
+    if (dtype == SGSPM_F64_DATA)
+        copy_out_kernel<T, double><<<nb, 256, 0, ctx->stream>>>((double*)ctx->d_stage, h0, h1, h2, nullptr, nullptr, nullptr,
+                                                                ctx->d_films, ctx->nfilm, n);
+    else
+        copy_out_kernel<T, float><<<nb, 256, 0, ctx->stream>>>((float*)ctx->d_stage, h0, h1, h2, nullptr, nullptr, nullptr,
+                                                               ctx->d_films, ctx->nfilm, n);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dL_dhe, ctx->d_stage, bytes, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(dL_dalpha, ctx->d_alpha_b, ctx->nfilm * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    // back to m(T)
+    if ((rc = state_io<T>(ctx, (T*)ctx->d_final, false))) return rc;
+    if ((rc = run_prog(ctx, ctx->fwd_prog, ctx->stream))) return rc;
     return check_status(ctx);
 }
 
@@ -1167,6 +1578,26 @@ int sgspm_energy_noalloc(const sgspm_grid* grid, double eps, double Q, const dou
 }
 
 const char* sgspm_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
+
+int sgspm_record(sgspm_t ctx, long long nsteps, int K) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (nsteps < 1 || K < 1) return fail(ctx, SGSPM_ERR_ARG, "nsteps and K must be >= 1");
+    if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
+    if (ctx->forcing) return fail(ctx, SGSPM_ERR_UNSUPPORTED, "recording with a manufactured forcing is not supported");
+    if (ctx->flags & (SGSPM_GSPM | SGSPM_FROZEN_STRAY))
+        return fail(ctx, SGSPM_ERR_UNSUPPORTED, "the adjoint covers SGSPM with f refreshed at every state");
+    if (K > nsteps) K = (int)nsteps;
+    return ctx->fp64 ? record_t<double>(ctx, nsteps, K) : record_t<float>(ctx, nsteps, K);
+}
+
+int sgspm_grad(sgspm_t ctx, const void* dL_dmT, int dtype, void* dL_dhe, double* dL_dalpha) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!dL_dmT || !dL_dhe || !dL_dalpha) return fail(ctx, SGSPM_ERR_ARG, "NULL argument");
+    if (dtype != SGSPM_F32 && dtype != SGSPM_F64_DATA) return fail(ctx, SGSPM_ERR_ARG, "dtype must be SGSPM_F32 or SGSPM_F64_DATA");
+    if (ctx->rec_nsteps < 1) return fail(ctx, SGSPM_ERR_STATE, "no recorded forward: call sgspm_record first");
+    return ctx->fp64 ? grad_t<double>(ctx, dL_dmT, dtype, dL_dhe, dL_dalpha)
+                     : grad_t<float>(ctx, dL_dmT, dtype, dL_dhe, dL_dalpha);
+}
 
 int sgspm_launches_per_step(sgspm_t ctx) {
     if (!ctx) return SGSPM_ERR_ARG;

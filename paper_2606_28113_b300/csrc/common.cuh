@@ -57,8 +57,8 @@ struct Film {
 };
 
 // Operand reference of a pointwise update: >= 0 real field slot, < 0 shared-memory slab (-1 - idx).
-constexpr int kMaxSlots = 24;
-constexpr int kMaxSpec = 8;
+constexpr int kMaxSlots = 64;
+constexpr int kMaxSpec = 12;
 
 // Slab (XZ) pass program.  Phases run in order; unused phases have count 0 / op 0.
 struct XZProg {
@@ -71,6 +71,7 @@ struct XZProg {
     int state[3];          // real slots of the state (m1, m2, m3) at which f is evaluated
     int damp;              // 0: scale = dt; 1: scale = alpha dt
     int rhs_dct;           // 0: only invert h_s (energy), no rhs / DCT
+    int rhs_copy[3];       // >= 0: the right-hand side is this slot as given (adjoint solves)
     // phase I: inverse DCT_xz of spectral-solved slots -> delta slabs in shared memory
     int n_inv;
     int inv_in[3];
@@ -80,6 +81,7 @@ struct XZProg {
     int gs_out, gs_base, gs_p, gs_q, gs_r, gs_s;   // out = base + p*q - r*s (operand refs)
     int fin_in[3];         // m** slots; delta slabs 0..2; m^{n+1} -> fin_out
     int fin_out[3];
+    int fin_v[3];          // >= 0: also store m*** (before projection) here (recorded steps)
     // phase F: forward zero-padded FFT (x R2C, z C2C) of real fields -> spectral slots
     int n_fwd;
     int fwd_src[3];        // operand refs (slab -1-idx means the phase-U result slab idx)
@@ -93,6 +95,7 @@ struct YProg {
     int slot[3];           // heat: real slots (in place); stray: output component a
     int damp;              // heat: 0 -> c = eps, 1 -> c = alpha eps
     int in_spec[3];        // stray: spectral slots of M_1, M_2, M_3
+    int in_mask;           // stray: bit b set if input component b is non-zero (others skipped)
     int out_spec[3];       // stray: spectral slot of H_a for each output
 };
 
@@ -112,9 +115,9 @@ struct Dev {
     const T* lam;          // eigenvalue pool
     const T* dtab;         // dense DCT tables of short axes
     const T* ktab;         // -N_hat / (Px Py Pz), reduced real table
-    T* field[kMaxSlots];
-    T* flo[kMaxSlots];     // low parts of double-float state slots (FP32 form), else null
-    cplx<T>* spec[kMaxSpec];
+    T* const* field;       // device table: real field slot -> pool pointer
+    T* const* flo;         // device table: low parts of double-float state slots (FP32 form), else null
+    cplx<T>* const* spec;  // device table: spectral slot -> pool pointer
     const T* he_cell;      // per-cell applied field [3][ncell_total] or null
     int* status;
     const long long* step_ctr;

@@ -98,7 +98,15 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     for (int ci = 0; ci < pg.n_rhs; ++ci) {
         const int a = pg.rhs_comp[ci];
         T* h = slabs;   // slab 0
-        if (pg.rhs_h[ci] >= 0 && stray) {
+        if (pg.rhs_copy[ci] >= 0) {
+            // the right-hand side is given (adjoint solves): copy it and transform
+            const T* src = d.field[pg.rhs_copy[ci]];
+            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                int z = idx / nx, x = idx - z * nx;
+                h[idx] = src[cell_of(z, x)];
+            }
+            __syncthreads();
+        } else if (pg.rhs_h[ci] >= 0 && stray) {
             const V* H = d.spec[pg.rhs_h[ci]] + sbase;
             if (zreg) {
                 // inverse zero-padded DFT along z in registers, one thread per kx column
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         }
         if (!pg.rhs_dct) { __syncthreads(); continue; }
         // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
-        {
+        if (pg.rhs_copy[ci] < 0) {
             const T* __restrict__ m1 = d.field[pg.state[0]];
             const T* __restrict__ m2 = d.field[pg.state[1]];
             const T* __restrict__ m3 = d.field[pg.state[2]];
@@ -391,6 +399,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     d.field[pg.fin_out[i]][c] = oh;
                     d.flo[pg.fin_out[i]][c] = ol;
                     slabs[i * S + idx] = oh;
+                    if (pg.fin_v[i] >= 0) d.field[pg.fin_v[i]][c] = h[i] + l[i];
                 }
                 continue;
             }
@@ -414,6 +423,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 T w = v[i] * inv;
                 d.field[pg.fin_out[i]][c] = w;
                 slabs[i * S + idx] = w;
+                if (pg.fin_v[i] >= 0) d.field[pg.fin_v[i]][c] = v[i];
             }
         }
         __syncthreads();
@@ -565,6 +575,7 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
     for (int o = 0; o < pg.n; ++o)
         for (int idx = threadIdx.x; idx < tn * LS; idx += blockDim.x) acc[o * B + idx] = cmk<V>(T(0), T(0));
     for (int b = 0; b < 3; ++b) {
+        if (!(pg.in_mask & (1 << b))) continue;
         const V* Sb = d.spec[pg.in_spec[b]] + F.off_spec + (long long)kz * ny * Kx + kx0;
         for (int idx = threadIdx.x; idx < tn * Py; idx += blockDim.x) {
             int yy = idx / tn, t = idx - yy * tn;
@@ -650,6 +661,7 @@ __device__ __forceinline__ void y_stray_line(const Dev<T>& d, const Film& F, con
     const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx;
 #pragma unroll 1
     for (int b = 0; b < 3; ++b) {
+        if (!(pg.in_mask & (1 << b))) continue;
         const V* Sb = d.spec[pg.in_spec[b]] + line0;
         V v[E];
 #pragma unroll

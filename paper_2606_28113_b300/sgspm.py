@@ -62,6 +62,10 @@ def lib():
     L.sgspm_launches_per_step.argtypes = [vp]
     L.sgspm_profile_step.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int), i]
     L.sgspm_version.argtypes = []
+    L.sgspm_record.argtypes = [vp, ll, i]
+    L.sgspm_record.restype = ctypes.c_int
+    L.sgspm_grad.argtypes = [vp, vp, i, vp, dp]
+    L.sgspm_grad.restype = ctypes.c_int
     L.sgspm_energy_noalloc.argtypes = [ctypes.POINTER(Grid), d, d, dp, dp, vp, vp, i, vp, vp]
     L.sgspm_energy_noalloc.restype = ctypes.c_int
     L.sgspm_noalloc_last_error.argtypes = []
@@ -236,6 +240,22 @@ class Handle:
         t = ctypes.c_double()
         self._check(lib().sgspm_get_time(self.h, ctypes.byref(t)))
         return t.value
+
+    def record(self, nsteps, K):
+        """Advance nsteps from the current m with a checkpoint every K steps (for grad)."""
+        self._check(lib().sgspm_record(self.h, int(nsteps), int(K)))
+
+    def grad(self, dL_dmT, out=None):
+        """Reverse sweep: returns (dL/dh_e, dL/dalpha per film) for dL/dm(T)."""
+        p, code, keep = _buffer(dL_dmT)
+        if out is None:
+            out = np.empty(3 * self.total_cells, dtype=np.float64 if code == F64 else np.float32)
+        q, code2, keep2 = _buffer(out)
+        if code2 != code:
+            raise ValueError("out must have the dtype of dL_dmT")
+        da = np.zeros(len(self.films))
+        self._check(lib().sgspm_grad(self.h, p, code, q, _dptr(da)))
+        return out, da
 
     def launches_per_step(self):
         return lib().sgspm_launches_per_step(self.h)
