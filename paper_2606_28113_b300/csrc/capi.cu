@@ -84,6 +84,14 @@ struct sgspm_ctx {
     int* d_status = nullptr;
     long long* d_step = nullptr;
     void* d_stage = nullptr;
+    // launches are split by size class: one instantiation of a pass per class of films
+    struct KClass {
+        int key;
+        int4* work;
+        int n;
+        size_t smem;
+    };
+    std::vector<KClass> xz_cls, yh_cls, yw_cls;
     int4* d_work_xz = nullptr;
     int n_xz = 0;
     int4* d_work_yh = nullptr;
@@ -191,23 +199,96 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
     return d;
 }
 
+// ---- size-class launchers -------------------------------------------------------------------
+static int pow2_key(int n, int lo, int hi) { return (n >= lo && n <= hi && (n & (n - 1)) == 0) ? n : 0; }
+
+template <typename T>
+static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray) {
+    if constexpr (sizeof(T) == 8) {   // the FP64 form uses the runtime-length kernel only
+        xz_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg, stray);
+        return;
+    }
+    switch (key) {
+#define SGSPM_XZ(K) case K: xz_kernel<T, K><<<nb, kThreads, smem, st>>>(d, w, pg, stray); break;
+        SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
+#undef SGSPM_XZ
+        default: xz_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg, stray);
+    }
+}
+template <typename T>
+static cudaError_t attr_xz(int key, size_t smem) {
+    if constexpr (sizeof(T) == 8) return cudaFuncSetAttribute(xz_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    switch (key) {
+#define SGSPM_XZ(K) case K: return cudaFuncSetAttribute(xz_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
+#undef SGSPM_XZ
+        default: return cudaFuncSetAttribute(xz_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+}
+template <typename T>
+static void launch_yh(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
+    if constexpr (sizeof(T) == 8) {
+        y_heat_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg);
+        return;
+    }
+    switch (key) {
+#define SGSPM_YH(K) case K: y_heat_kernel<T, K><<<nb, kThreads, smem, st>>>(d, w, pg); break;
+        SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
+#undef SGSPM_YH
+        default: y_heat_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg);
+    }
+}
+template <typename T>
+static cudaError_t attr_yh(int key, size_t smem) {
+    if constexpr (sizeof(T) == 8) return cudaFuncSetAttribute(y_heat_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    switch (key) {
+#define SGSPM_YH(K) case K: return cudaFuncSetAttribute(y_heat_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
+#undef SGSPM_YH
+        default: return cudaFuncSetAttribute(y_heat_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+}
+// key = E = Py / 32
+template <typename T, int NOUT>
+static void launch_yw_n(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
+    const unsigned nt = 32 * kWarpLines;
+    switch (key) {
+        case 2: y_stray_warp_kernel<T, NOUT, 2><<<nb, nt, smem, st>>>(d, w, pg); break;
+        case 4: y_stray_warp_kernel<T, NOUT, 4><<<nb, nt, smem, st>>>(d, w, pg); break;
+        case 8: y_stray_warp_kernel<T, NOUT, 8><<<nb, nt, smem, st>>>(d, w, pg); break;
+        default: y_stray_warp_kernel<T, NOUT, 16><<<nb, nt, smem, st>>>(d, w, pg); break;
+    }
+}
+template <typename T>
+static void launch_yw(int key, int nout, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
+    if (nout == 1) launch_yw_n<T, 1>(key, nb, smem, st, d, w, pg);
+    else if (nout == 2) launch_yw_n<T, 2>(key, nb, smem, st, d, w, pg);
+    else launch_yw_n<T, 3>(key, nb, smem, st, d, w, pg);
+}
+template <typename T, int NOUT>
+static cudaError_t attr_yw_n(int key, size_t smem) {
+    switch (key) {
+        case 2: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 4: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 8: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        default: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+}
+
 template <typename T>
 static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
     Dev<T> d = dev_view<T>(ctx);
     switch (L.kind) {
         case 0:
-            xz_kernel<T><<<ctx->n_xz, kThreads, ctx->smem_xz, st>>>(d, ctx->d_work_xz, L.xz, ctx->stray ? 1 : 0);
+            for (const auto& c : ctx->xz_cls) launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0);
             break;
         case 1:
-            y_heat_kernel<T><<<ctx->n_yh, kThreads, ctx->smem_yh, st>>>(d, ctx->d_work_yh, L.y);
+            for (const auto& c : ctx->yh_cls) launch_yh<T>(c.key, c.n, c.smem, st, d, c.work, L.y);
             break;
         case 2: {
             int n = L.y.n;
             if (ctx->warp_stray) {
-                const unsigned nb = (unsigned)ctx->n_yw, nt = 32 * kWarpLines;
-                if (n == 1) y_stray_warp_kernel<T, 1><<<nb, nt, ctx->smem_yw, st>>>(d, ctx->d_work_yw, L.y);
-                else if (n == 2) y_stray_warp_kernel<T, 2><<<nb, nt, ctx->smem_yw, st>>>(d, ctx->d_work_yw, L.y);
-                else y_stray_warp_kernel<T, 3><<<nb, nt, ctx->smem_yw, st>>>(d, ctx->d_work_yw, L.y);
+                for (const auto& c : ctx->yw_cls) launch_yw<T>(c.key, n, c.n, c.smem, st, d, c.work, L.y);
             } else {
                 y_stray_kernel<T><<<ctx->n_ys[n], kThreads, ctx->smem_ys[n], st>>>(d, ctx->d_work_ys[n], L.y, ctx->tx_s[n]);
             }
@@ -900,6 +981,34 @@ static int setup_t(sgspm_ctx* ctx) {
         F.plan_px = ids[3];
         F.plan_py = ids[4];
         F.plan_pz = ids[5];
+        {
+            // copies: staged() below grows ctx->plans
+            const Plan dx = ctx->plans[ids[0]], dy = ctx->plans[ids[1]], dz = ctx->plans[ids[2]];
+            const Plan px = ctx->plans[ids[3]], py = ctx->plans[ids[4]], pz = ctx->plans[ids[5]];
+            F.gtw_dx = dx.tw;
+            F.gtw4_dx = dx.tw4;
+            F.gtw_dz = dz.tw;
+            F.gtw4_dz = dz.tw4;
+            F.gtw_px = px.tw;
+            F.gtw_pz = pz.tw;
+            F.gtw_dy = dy.tw;
+            F.gtw4_dy = dy.tw4;
+            F.gtw_py = py.tw;
+            F.gdtab_z = dz.dtab >= 0 ? dz.dtab : 0;
+            auto staged = [&](const Plan& src, int tw, int tw4) {
+                Plan q = src;
+                q.tw = tw;
+                q.tw4 = tw4;
+                ctx->plans.push_back(q);
+                return (int)ctx->plans.size() - 1;
+            };
+            const int nx = F.nx, nz = F.nz;
+            F.splan_dx = staged(dx, 0, nx);
+            F.splan_dz = staged(dz, 2 * nx, 2 * nx + nz);
+            F.splan_px = staged(px, 2 * nx + 2 * nz, 0);
+            F.splan_pz = staged(pz, 2 * nx + 2 * nz + F.Px, 0);
+            F.splan_dy = staged(dy, 0, F.ny);
+        }
         F.off_cell = oc;
         oc += (long long)F.nx * F.ny * F.nz;
         F.off_spec = os;
@@ -959,34 +1068,49 @@ static int setup_t(sgspm_ctx* ctx) {
         if (ctx->smem_ys[n] > (size_t)smem_max)
             return fail(ctx, SGSPM_ERR_UNSUPPORTED, "y line of length " + std::to_string(maxPy) + " does not fit in shared memory");
     }
-    CK(cudaFuncSetAttribute(xz_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_xz));
-    CK(cudaFuncSetAttribute(y_heat_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yh));
     CK(cudaFuncSetAttribute(y_stray_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)std::max(ctx->smem_ys[1], std::max(ctx->smem_ys[2], ctx->smem_ys[3]))));
-    // work lists
-    std::vector<int4> wx, wy, we;
+    // work lists: slab and heat passes per size class (films of one x / y length share a launch)
+    std::vector<int4> we;
     std::vector<int> first_e;
-    for (int f = 0; f < ctx->nfilm; ++f) {
-        const Film& F = ctx->films[f];
-        for (int y = 0; y < F.ny; ++y) wx.push_back(make_int4(f, y, 0, 0));
-        for (int kz = 0; kz < F.nz; ++kz)
-            for (int x0 = 0; x0 < F.nx; x0 += ctx->tx_h) wy.push_back(make_int4(f, kz, x0, std::min(ctx->tx_h, F.nx - x0)));
-        first_e.push_back((int)we.size());
-        long long nc = (long long)F.nx * F.ny * F.nz;
-        for (long long c0 = 0; c0 < nc; c0 += 4096) we.push_back(make_int4(f, (int)c0, (int)std::min(4096LL, nc - c0), 0));
-    }
-    first_e.push_back((int)we.size());
     auto up4 = [&](int4** d, const std::vector<int4>& h) -> int {
         CK(cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(int4)));
         if (!h.empty()) CK(cudaMemcpy(*d, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice));
         return SGSPM_OK;
     };
     int rc;
-    if ((rc = up4(&ctx->d_work_xz, wx))) return rc;
-    if ((rc = up4(&ctx->d_work_yh, wy))) return rc;
+    {
+        std::map<int, std::vector<int4>> wx, wy;
+        std::map<int, size_t> sxk, syk;
+        for (int f = 0; f < ctx->nfilm; ++f) {
+            const Film& F = ctx->films[f];
+            const int kx = sizeof(T) == 8 ? 0 : pow2_key(F.nx, 8, 512), ky = sizeof(T) == 8 ? 0 : pow2_key(F.ny, 8, 512);
+            for (int y = 0; y < F.ny; ++y) wx[kx].push_back(make_int4(f, y, 0, 0));
+            for (int kz = 0; kz < F.nz; ++kz)
+                for (int x0 = 0; x0 < F.nx; x0 += ctx->tx_h) wy[ky].push_back(make_int4(f, kz, x0, std::min(ctx->tx_h, F.nx - x0)));
+            XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray);
+            sxk[kx] = std::max(sxk[kx], xz_smem_bytes<T>(L));
+            syk[ky] = std::max(syk[ky], (size_t)2 * F.ny * V + (size_t)2 * ((ctx->tx_h + 1) / 2) * F.ny * V +
+                                            (size_t)ctx->tx_h * (F.ny + 8) * sizeof(T));
+            first_e.push_back((int)we.size());
+            long long nc = (long long)F.nx * F.ny * F.nz;
+            for (long long c0 = 0; c0 < nc; c0 += 4096) we.push_back(make_int4(f, (int)c0, (int)std::min(4096LL, nc - c0), 0));
+        }
+        for (auto& kv : wx) {
+            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), sxk[kv.first]};
+            if ((rc = up4(&c.work, kv.second))) return rc;
+            CK(attr_xz<T>(c.key, c.smem));
+            ctx->xz_cls.push_back(c);
+        }
+        for (auto& kv : wy) {
+            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), syk[kv.first]};
+            if ((rc = up4(&c.work, kv.second))) return rc;
+            CK(attr_yh<T>(c.key, c.smem));
+            ctx->yh_cls.push_back(c);
+        }
+    }
+    first_e.push_back((int)we.size());
     if ((rc = up4(&ctx->d_work_e, we))) return rc;
-    ctx->n_xz = (int)wx.size();
-    ctx->n_yh = (int)wy.size();
     ctx->n_e = (int)we.size();
     for (int n = 1; n <= 3; ++n) {
         std::vector<int4> ws;
@@ -998,23 +1122,28 @@ static int setup_t(sgspm_ctx* ctx) {
         if ((rc = up4(&ctx->d_work_ys[n], ws))) return rc;
         ctx->n_ys[n] = (int)ws.size();
     }
-    // register-resident stray pass when every film's padded y length is 64..512
+    // register-resident stray pass when every film's padded y length is 64..512, per length class
     ctx->warp_stray = ctx->stray;
     for (const Film& F : ctx->films)
         if (!(F.Py == 64 || F.Py == 128 || F.Py == 256 || F.Py == 512)) ctx->warp_stray = false;
     if (ctx->warp_stray) {
-        std::vector<int4> ws;
+        std::map<int, std::vector<int4>> ws;
         for (int f = 0; f < ctx->nfilm; ++f) {
             const Film& F = ctx->films[f];
             for (int kz = 0; kz < F.Pz; ++kz)
-                for (int x0 = 0; x0 < F.Kx; x0 += kWarpLines) ws.push_back(make_int4(f, kz, x0, std::min(kWarpLines, F.Kx - x0)));
+                for (int x0 = 0; x0 < F.Kx; x0 += kWarpLines)
+                    ws[F.Py / 32].push_back(make_int4(f, kz, x0, std::min(kWarpLines, F.Kx - x0)));
         }
-        if ((rc = up4(&ctx->d_work_yw, ws))) return rc;
-        ctx->n_yw = (int)ws.size();
-        ctx->smem_yw = (size_t)(1 + kWarpLines) * maxPy * V;
-        CK(cudaFuncSetAttribute(y_stray_warp_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yw));
-        CK(cudaFuncSetAttribute(y_stray_warp_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yw));
-        CK(cudaFuncSetAttribute(y_stray_warp_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_yw));
+        for (auto& kv : ws) {
+            const size_t smem = (size_t)(1 + kWarpLines) * 32 * kv.first * V;
+            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), smem};
+            if ((rc = up4(&c.work, kv.second))) return rc;
+            cudaError_t e1 = attr_yw_n<T, 1>(c.key, smem), e2 = attr_yw_n<T, 2>(c.key, smem), e3 = attr_yw_n<T, 3>(c.key, smem);
+            CK(e1);
+            CK(e2);
+            CK(e3);
+            ctx->yw_cls.push_back(c);
+        }
     }
     CK(cudaMalloc(&ctx->d_first_e, first_e.size() * sizeof(int)));
     CK(cudaMemcpy(ctx->d_first_e, first_e.data(), first_e.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1083,6 +1212,9 @@ static void release(sgspm_ctx* ctx) {
         if (p) cudaFree(p);
     for (int n = 0; n < 4; ++n)
         if (ctx->d_work_ys[n]) cudaFree(ctx->d_work_ys[n]);
+    for (auto* v : {&ctx->xz_cls, &ctx->yh_cls, &ctx->yw_cls})
+        for (auto& c : *v)
+            if (c.work) cudaFree(c.work);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
 }
 
@@ -1598,6 +1730,19 @@ int sgspm_grad(sgspm_t ctx, const void* dL_dmT, int dtype, void* dL_dhe, double*
     return ctx->fp64 ? grad_t<double>(ctx, dL_dmT, dtype, dL_dhe, dL_dalpha)
                      : grad_t<float>(ctx, dL_dmT, dtype, dL_dhe, dL_dalpha);
 }
+
+#ifdef SGSPM_PHASE_TIMING
+// instrumented builds only: clock64 stamps of block 0 of the last slab pass
+int sgspm_debug_phase_clk(long long* out) {
+    cudaDeviceSynchronize();
+    return cudaMemcpyFromSymbol(out, g_phase_clk, 64 * sizeof(long long)) == cudaSuccess ? 0 : -3;
+}
+int sgspm_debug_run_launch(sgspm_t ctx, int i) {
+    int rc = enqueue(ctx, ctx->step_prog[i], ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return rc ? rc : ctx->step_prog[i].kind * 10 + (ctx->step_prog[i].kind == 0 ? (ctx->step_prog[i].xz.n_rhs ? 1 : ctx->step_prog[i].xz.op == 2 ? 3 : 2) : ctx->step_prog[i].y.n);
+}
+#endif
 
 int sgspm_launches_per_step(sgspm_t ctx) {
     if (!ctx) return SGSPM_ERR_ARG;

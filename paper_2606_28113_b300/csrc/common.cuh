@@ -49,6 +49,11 @@ struct Film {
     int plan_dx, plan_dy, plan_dz;   // DCT lengths nx, ny, nz
     int plan_px, plan_py, plan_pz;   // padded lengths Px, Py, Pz
     int forcing;             // 0 none, 1 MMS 1D, 3 MMS 3D
+    // plans whose twiddle offsets refer to the shared-memory staging layout of the passes:
+    // slab pass [W_nx | W4_nx | W_nz | W4_nz | W_Px | W_Pz], heat line pass [W_ny | W4_ny]
+    int splan_dx, splan_dz, splan_px, splan_pz, splan_dy;
+    // global offsets of the same tables in the twiddle pool, and of the short-axis DCT table
+    int gtw_dx, gtw4_dx, gtw_dz, gtw4_dz, gtw_px, gtw_pz, gtw_dy, gtw4_dy, gtw_py, gdtab_z;
     double hx, hy, hz;
     double eps, Q, alpha, dt;
     double u[3];

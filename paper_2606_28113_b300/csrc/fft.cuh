@@ -408,6 +408,22 @@ __device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, c
     return a;
 }
 
+// FFT of all lines with the length known at compile time (PC > 0), or the runtime path (PC = 0).
+template <typename T, bool INV, int PC>
+__device__ __forceinline__ cplx<T>* fft_lines_t(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, const cplx<T>* __restrict__ twpool) {
+    if constexpr (PC == 0) {
+        return fft_lines<T, INV>(a, b, L, pl, twpool);
+    } else if constexpr (PC == 1) {
+        return a;
+    } else {
+        const cplx<T>* tw = twpool + pl.tw;
+        if constexpr (PC >= 64 && PC <= 512) {
+            if (L.es == 1 && L.ls >= PC) return warp_fft<T, INV, PC / 32>(a, b, L, tw);
+        }
+        return ct_fft<T, INV, PC>(a, b, L, tw);
+    }
+}
+
 // Makhoul permutation: position of input sample j in the reordered sequence v.
 __device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
 // inverse: sample index stored at position n of v
@@ -415,7 +431,7 @@ __device__ __forceinline__ int mk_src(int n, int N) { return (n < (N + 1) / 2) ?
 
 // Unnormalised DCT-II  X_k = sum_n x_n cos(pi k (2n+1) / (2N))  of L real lines (in place).
 // R: real lines (R.ls / R.es strides, length N).  ca, cb: complex scratch of >= ceil(L/2) * N.
-template <typename T>
+template <typename T, int PC = 0>
 __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const Plan& pl,
                            const cplx<T>* __restrict__ twpool) {
     using V = cplx<T>;
@@ -428,7 +444,7 @@ __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
         ca[p * N + mk_pos(j, N)] = cmk<V>(re, im);
     }
     __syncthreads();
-    V* res = fft_lines<T, false>(ca, cb, C, pl, twpool);
+    V* res = fft_lines_t<T, false, PC>(ca, cb, C, pl, twpool);
     const V* w4 = twpool + pl.tw4;
     for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
         int p = idx / N, k = idx - p * N;
@@ -444,7 +460,7 @@ __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
 }
 
 // Inverse of dct2_lines up to a factor N (the caller folds 1/N into its scaling).
-template <typename T>
+template <typename T, int PC = 0>
 __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const Plan& pl,
                            const cplx<T>* __restrict__ twpool) {
     using V = cplx<T>;
@@ -464,7 +480,7 @@ __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
         ca[p * N + k] = cmk<V>(va.x - vb.y, va.y + vb.x);
     }
     __syncthreads();
-    V* res = fft_lines<T, true>(ca, cb, C, pl, twpool);
+    V* res = fft_lines_t<T, true, PC>(ca, cb, C, pl, twpool);
     for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
         int p = idx / N, n = idx - p * N;
         V z = res[p * N + n];
@@ -478,7 +494,7 @@ __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
 // Zero-padded FFT of length P of L real lines of length nlen (P = 2 nlen, or 1).
 // Leaves the packed complex transform of line pairs in the returned buffer, layout
 // [pair][P]; extract line spectra with r2c_get.
-template <typename T>
+template <typename T, int PC = 0>
 __device__ cplx<T>* r2c_lines(const T* R, Lines L, int nlen, cplx<T>* ca, cplx<T>* cb, const Plan& pl,
                               const cplx<T>* __restrict__ twpool) {
     using V = cplx<T>;
@@ -494,7 +510,7 @@ __device__ cplx<T>* r2c_lines(const T* R, Lines L, int nlen, cplx<T>* ca, cplx<T
         ca[p * P + j] = v;
     }
     __syncthreads();
-    return fft_lines<T, false>(ca, cb, Lines{npair, P, 1}, pl, twpool);
+    return fft_lines_t<T, false, PC>(ca, cb, Lines{npair, P, 1}, pl, twpool);
 }
 
 // Spectrum X_line[k], k in [0, P/2], of one real line from the packed pair transform.

@@ -36,13 +36,36 @@ __device__ inline void mms_forcing(int dim, double x, double y, double z, double
     for (int i = 0; i < 3; ++i) fe[i] = dtm[i] + mxl[i] + alpha * mmxl[i];
 }
 
+// Length-P DFT of a column held in registers (P a power of two <= 2 kZReg); false otherwise.
+template <typename T, bool INV>
+__device__ __forceinline__ bool zfft_reg(cplx<T> (&v)[2 * kZReg], int P) {
+    using V = cplx<T>;
+    switch (P) {
+        case 16: Bfly<16, INV, V>::run(v); return true;
+        case 8: Bfly<8, INV, V>::run(v); return true;
+        case 4: Bfly<4, INV, V>::run(v); return true;
+        case 2: Bfly<2, INV, V>::run(v); return true;
+        case 1: return true;
+        default: return false;
+    }
+}
+
+#ifdef SGSPM_PHASE_TIMING
+__device__ long long g_phase_clk[64];
+#define PHASE_MARK(k) do { if (blockIdx.x == 0 && threadIdx.x == 0) g_phase_clk[k] = clock64(); } while (0)
+#else
+#define PHASE_MARK(k) do { } while (0)
+#endif
+
 // ------------------------------------------------------------------------------------------
 // XZ slab pass
 // ------------------------------------------------------------------------------------------
-template <typename T>
+// NX: compile-time x length of the films this launch covers (0: any length, runtime transforms)
+template <typename T, int NX>
 __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    PHASE_MARK(14);
     const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
     const int y = wi.y;
@@ -50,19 +73,22 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0);
     __shared__ Plan pdx, pdz, ppx, ppz;
     if (threadIdx.x == 0) {
-        pdx = d.plans[F.plan_dx];
-        pdz = d.plans[F.plan_dz];
-        ppx = d.plans[F.plan_px];
-        ppz = d.plans[F.plan_pz];
+        // pre-staged plan copies (their twiddle offsets refer to the shared layout below)
+        pdx = d.plans[F.splan_dx];
+        pdz = d.plans[F.splan_dz];
+        ppx = d.plans[F.splan_px];
+        ppz = d.plans[F.splan_pz];
     }
-    __syncthreads();
     // staged twiddles: [W_nx | W4_nx | W_nz | W4_nz | W_Px | W_Pz], then the short-axis DCT tables
     V* stw = reinterpret_cast<V*>(smem_raw);
-    stage_plan<T>(pdx, d.tw, stw, 0, true);
-    stage_plan<T>(pdz, d.tw, stw, 2 * nx, true);
-    if (stray) {
-        stage_plan<T>(ppx, d.tw, stw, 2 * nx + 2 * nz, false);
-        stage_plan<T>(ppz, d.tw, stw, 2 * nx + 2 * nz + Px, false);
+    {
+        const int segs[6] = {F.gtw_dx, F.gtw4_dx, F.gtw_dz, F.gtw4_dz, F.gtw_px, F.gtw_pz};
+        const int lens[6] = {nx, nx, nz, nz, stray ? Px : 0, stray ? Pz : 0};
+        int off = 0;
+        for (int k = 0; k < 6; ++k) {
+            for (int i = threadIdx.x; i < lens[k]; i += blockDim.x) stw[off + i] = d.tw[segs[k] + i];
+            off += lens[k];
+        }
     }
     V* xw0 = stw + Lo.tw;
     V* xw1 = xw0 + Lo.xw;
@@ -71,16 +97,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     T* slabs = reinterpret_cast<T*>(zw1 + Lo.zw);
     T* sdt = slabs + 3 * Lo.slab;
     if (Lo.dt)
-        for (int i = threadIdx.x; i < 2 * nz * nz; i += blockDim.x) sdt[i] = d.dtab[pdz.dtab + i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        pdx.tw = 0;
-        pdx.tw4 = nx;
-        pdz.tw = 2 * nx;
-        pdz.tw4 = 2 * nx + nz;
-        ppx.tw = 2 * nx + 2 * nz;
-        ppz.tw = 2 * nx + 2 * nz + Px;
-    }
+        for (int i = threadIdx.x; i < 2 * nz * nz; i += blockDim.x) sdt[i] = d.dtab[F.gdtab_z + i];
     __syncthreads();
     const int S = Lo.slab;
     const int KC = Lo.kc;
@@ -89,6 +106,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     const long long cbase = F.off_cell;
     const long long sbase = F.off_spec;
     auto cell_of = [&](int z, int x) -> long long { return cbase + ((long long)z * ny + y) * nx + x; };
+    PHASE_MARK(0);
     const bool zreg = z_in_registers(nz);
     const T* Cz = sdt;                                       // DCT-II  C[k][n]
     const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
@@ -118,16 +136,21 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
 #pragma unroll
                     for (int kz = 0; kz < 2 * kZReg; ++kz)
                         hz[kz] = kz < Pz ? H[((long long)kz * ny + y) * Kx + kx] : cmk<V>(T(0), T(0));
+                    if (zfft_reg<T, true>(hz, Pz)) {
 #pragma unroll
-                    for (int kz = 0; kz < 2 * kZReg; ++kz) {
-                        if (kz >= Pz) break;
-                        const V hv = hz[kz];
-                        int m = 0;
+                        for (int z = 0; z < kZReg; ++z) acc[z] = hz[z];
+                    } else {
 #pragma unroll
-                        for (int z = 0; z < kZReg; ++z) {
-                            if (z < nz) acc[z] = cadd(acc[z], cmul(hv, cconj(twz[m])));
-                            m += kz;
-                            if (m >= Pz) m -= Pz;
+                        for (int kz = 0; kz < 2 * kZReg; ++kz) {
+                            if (kz >= Pz) break;
+                            const V hv = hz[kz];
+                            int m = 0;
+#pragma unroll
+                            for (int z = 0; z < kZReg; ++z) {
+                                if (z < nz) acc[z] = cadd(acc[z], cmul(hv, cconj(twz[m])));
+                                m += kz;
+                                if (m >= Pz) m -= Pz;
+                            }
                         }
                     }
 #pragma unroll
@@ -152,7 +175,9 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 }
                 __syncthreads();
             }
-            V* r = fft_lines<T, true>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
+            PHASE_MARK(1);
+            V* r = fft_lines_t<T, true, 2 * NX>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
+            PHASE_MARK(2);
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
                 int z = idx / nx, x = idx - z * nx;
                 V v = r[(z >> 1) * Px + x];
@@ -169,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 out[cell_of(z, x)] = h[idx];
             }
         }
+        PHASE_MARK(3);
         if (!pg.rhs_dct) { __syncthreads(); continue; }
         // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
         if (pg.rhs_copy[ci] < 0) {
@@ -176,7 +202,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             const T* __restrict__ m2 = d.field[pg.state[1]];
             const T* __restrict__ m3 = d.field[pg.state[2]];
             const T* __restrict__ ma = d.field[pg.state[a]];
-            const T* __restrict__ ml = d.flo[pg.state[a]];   // low part (double-float state) or null
             const T scale = T(pg.damp ? F.alpha * F.dt : F.dt);
             const T eps = T(F.eps), Q = T(F.Q);
             const T ux = T(F.u[0]), uy = T(F.u[1]), uz = T(F.u[2]);
@@ -187,7 +212,9 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             // batches of kB cells per thread: every load of the batch is issued before any use
             constexpr int kB = sizeof(T) == 4 ? 4 : 2;
             for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
-                T v1[kB], v2[kB], v3[kB], mc[kB], mcl[kB], nb[kB][6], nl[kB][6];
+                // the stencil reads the hi part of a double-float state: its neighbour differences are
+                // O(h^2 |Delta m|) and the lo parts change them below the FP32 operator rounding
+                T v1[kB], v2[kB], v3[kB], mc[kB], nb[kB][6];
 #pragma unroll
                 for (int u = 0; u < kB; ++u) {
                     const int idx = i0 + u * blockDim.x;
@@ -198,15 +225,11 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     v2[u] = m2[c];
                     v3[u] = m3[c];
                     mc[u] = ma[c];
-                    mcl[u] = ml ? ml[c] : T(0);
                     // neighbours with mirror ghosts (a missing neighbour repeats the cell)
                     const long long o[6] = {x + 1 < nx ? 1 : 0, x > 0 ? -1 : 0, y + 1 < ny ? (long long)nx : 0,
                                             y > 0 ? -(long long)nx : 0, z + 1 < nz ? sz : 0, z > 0 ? -sz : 0};
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        nb[u][k] = ma[c + o[k]];
-                        nl[u][k] = ml ? ml[c + o[k]] : T(0);
-                    }
+                    for (int k = 0; k < 6; ++k) nb[u][k] = ma[c + o[k]];
                 }
 #pragma unroll
                 for (int u = 0; u < kB; ++u) {
@@ -216,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     const T mu = v1[u] * ux + v2[u] * uy + v3[u] * uz;
                     T d6[6];
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) d6[k] = (nb[u][k] - mc[u]) + (nl[u][k] - mcl[u]);
+                    for (int k = 0; k < 6; ++k) d6[k] = nb[u][k] - mc[u];
                     const T lap = ihx * (d6[0] + d6[1]) + ihy * (d6[2] + d6[3]) + ihz * (d6[4] + d6[5]);
                     const T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
                     const T f = -Q * (mc[u] - mu * ua) + h[idx] + he;
@@ -225,7 +248,9 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             }
         }
         __syncthreads();
-        dct2_lines<T>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
+        PHASE_MARK(4);
+        dct2_lines<T, NX>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
+        PHASE_MARK(5);
         if (zreg) {
             for (int x = threadIdx.x; x < nx; x += blockDim.x) {
                 T v[kZReg];
@@ -255,6 +280,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         __syncthreads();
     }
 
+    PHASE_MARK(6);
     // ---- phase I: inverse DCT of solved spectra -> delta slabs ------------------------------
     for (int i = 0; i < pg.n_inv; ++i) {
         T* s = slabs + i * S;
@@ -283,7 +309,9 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         } else {
             dct3_lines<T>(s, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
         }
-        dct3_lines<T>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
+        PHASE_MARK(7);
+        dct3_lines<T, NX>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
+        PHASE_MARK(8);
         if (pg.inv_store[i] >= 0) {
             T* out = d.field[pg.inv_store[i]];
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
@@ -293,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         }
     }
 
+    PHASE_MARK(9);
     // ---- phase U: pointwise updates ----------------------------------------------------------
     if (pg.op == 1) {
         // Gauss-Seidel cross product: out = base + p*q - r*s  (delta form, see host program)
@@ -429,6 +458,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         __syncthreads();
     }
 
+    PHASE_MARK(10);
     // ---- phase F: forward zero-padded FFT (x R2C, z C2C) -> spectral slots ---------------------
     if (stray) {
         for (int i = 0; i < pg.n_fwd; ++i) {
@@ -446,24 +476,32 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             } else {
                 src = slabs + (-1 - ref) * S;
             }
-            V* r = r2c_lines<T>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
+            PHASE_MARK(11);
+            V* r = r2c_lines<T, 2 * NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
+            PHASE_MARK(12);
             V* out = d.spec[pg.fwd_dst[i]] + sbase;
             if (zreg) {
                 // zero-padded DFT along z in registers, one thread per kx column
                 for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
-                    V v[kZReg];
+                    V v[2 * kZReg];
 #pragma unroll
-                    for (int z = 0; z < kZReg; ++z) v[z] = z < nz ? r2c_get<T>(r, z, kx, Px) : cmk<V>(T(0), T(0));
-                    for (int kz = 0; kz < Pz; ++kz) {
-                        V acc = cmk<V>(T(0), T(0));
-                        int m = 0;
+                    for (int z = 0; z < 2 * kZReg; ++z) v[z] = z < nz ? r2c_get<T>(r, z, kx, Px) : cmk<V>(T(0), T(0));
+                    if (zfft_reg<T, false>(v, Pz)) {
 #pragma unroll
-                        for (int z = 0; z < kZReg; ++z) {
-                            if (z < nz) acc = cadd(acc, cmul(v[z], twz[m]));
-                            m += kz;
-                            if (m >= Pz) m -= Pz;
+                        for (int kz = 0; kz < 2 * kZReg; ++kz)
+                            if (kz < Pz) out[((long long)kz * ny + y) * Kx + kx] = v[kz];
+                    } else {
+                        for (int kz = 0; kz < Pz; ++kz) {
+                            V acc = cmk<V>(T(0), T(0));
+                            int m = 0;
+#pragma unroll
+                            for (int z = 0; z < kZReg; ++z) {
+                                if (z < nz) acc = cadd(acc, cmul(v[z], twz[m]));
+                                m += kz;
+                                if (m >= Pz) m -= Pz;
+                            }
+                            out[((long long)kz * ny + y) * Kx + kx] = acc;
                         }
-                        out[((long long)kz * ny + y) * Kx + kx] = acc;
                     }
                 }
                 __syncthreads();
@@ -484,12 +522,14 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             }
         }
     }
+    PHASE_MARK(13);
 }
 
 // ------------------------------------------------------------------------------------------
 // Y line pass
 // ------------------------------------------------------------------------------------------
-template <typename T>
+// NY: compile-time y length of the films this launch covers (0: any length)
+template <typename T, int NY>
 __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -498,14 +538,11 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
     const int kz = wi.y, kx0 = wi.z, tn = wi.w;
     const int nx = F.nx, ny = F.ny, nz = F.nz;
     __shared__ Plan pdy;
-    if (threadIdx.x == 0) pdy = d.plans[F.plan_dy];
-    __syncthreads();
+    if (threadIdx.x == 0) pdy = d.plans[F.splan_dy];   // staged copy: twiddles at 0, quarter-wave at ny
     V* stw = reinterpret_cast<V*>(smem_raw);
-    stage_plan<T>(pdy, d.tw, stw, 0, true);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        pdy.tw = 0;
-        pdy.tw4 = ny;
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) {
+        stw[i] = d.tw[F.gtw_dy + i];
+        stw[ny + i] = d.tw[F.gtw4_dy + i];
     }
     __syncthreads();
     const int npair = (tn + 1) / 2;
@@ -525,13 +562,13 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
             R[t * LR + yy] = g[(long long)yy * nx + t];
         }
         __syncthreads();
-        dct2_lines<T>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
+        dct2_lines<T, NY>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
         for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
             int t = idx / ny, ky = idx - t * ny;
             R[t * LR + ky] *= norm / (T(1) + c * (lx[kx0 + t] + ly[ky] + lzv));
         }
         __syncthreads();
-        dct3_lines<T>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
+        dct3_lines<T, NY>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
         for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
             int yy = idx / tn, t = idx - yy * tn;
             g[(long long)yy * nx + t] = R[t * LR + yy];
@@ -701,7 +738,7 @@ __device__ __forceinline__ void y_stray_line(const Dev<T>& d, const Film& F, con
 
 constexpr int kWarpLines = 4;   // kx lines (warps) per CTA of the register stray pass
 
-template <typename T, int NOUT>
+template <typename T, int NOUT, int E>
 __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -719,12 +756,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     if (warp >= tn) return;
     V* scr = stw + Py + warp * Py;
     const int kx = kx0 + warp;
-    switch (Py) {
-        case 64: y_stray_line<T, NOUT, 2>(d, F, pg, kz, kx, scr, stw, lane); break;
-        case 128: y_stray_line<T, NOUT, 4>(d, F, pg, kz, kx, scr, stw, lane); break;
-        case 256: y_stray_line<T, NOUT, 8>(d, F, pg, kz, kx, scr, stw, lane); break;
-        default: y_stray_line<T, NOUT, 16>(d, F, pg, kz, kx, scr, stw, lane); break;
-    }
+    y_stray_line<T, NOUT, E>(d, F, pg, kz, kx, scr, stw, lane);
 }
 
 // ------------------------------------------------------------------------------------------
