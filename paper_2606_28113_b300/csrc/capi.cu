@@ -200,19 +200,35 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
 }
 
 // ---- size-class launchers -------------------------------------------------------------------
+// Pass kernels are launched with programmatic stream serialization (see pdl_wait in the kernels).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 static int pow2_key(int n, int lo, int hi) { return (n >= lo && n <= hi && (n & (n - 1)) == 0) ? n : 0; }
 
 template <typename T>
 static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray) {
     if constexpr (sizeof(T) == 8) {   // the FP64 form uses the runtime-length kernel only
-        xz_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg, stray);
+        launch_pdl(xz_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg, stray);
         return;
     }
     switch (key) {
-#define SGSPM_XZ(K) case K: xz_kernel<T, K><<<nb, kThreads, smem, st>>>(d, w, pg, stray); break;
+#define SGSPM_XZ(K) case K: launch_pdl(xz_kernel<T, K>, nb, kThreads, smem, st, d, w, pg, stray); break;
         SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
 #undef SGSPM_XZ
-        default: xz_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg, stray);
+        default: launch_pdl(xz_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg, stray);
     }
 }
 template <typename T>
@@ -228,14 +244,14 @@ static cudaError_t attr_xz(int key, size_t smem) {
 template <typename T>
 static void launch_yh(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
     if constexpr (sizeof(T) == 8) {
-        y_heat_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg);
+        launch_pdl(y_heat_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg);
         return;
     }
     switch (key) {
-#define SGSPM_YH(K) case K: y_heat_kernel<T, K><<<nb, kThreads, smem, st>>>(d, w, pg); break;
+#define SGSPM_YH(K) case K: launch_pdl(y_heat_kernel<T, K>, nb, kThreads, smem, st, d, w, pg); break;
         SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
 #undef SGSPM_YH
-        default: y_heat_kernel<T, 0><<<nb, kThreads, smem, st>>>(d, w, pg);
+        default: launch_pdl(y_heat_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg);
     }
 }
 template <typename T>
@@ -253,10 +269,10 @@ template <typename T, int NOUT>
 static void launch_yw_n(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
     const unsigned nt = 32 * kWarpLines;
     switch (key) {
-        case 2: y_stray_warp_kernel<T, NOUT, 2><<<nb, nt, smem, st>>>(d, w, pg); break;
-        case 4: y_stray_warp_kernel<T, NOUT, 4><<<nb, nt, smem, st>>>(d, w, pg); break;
-        case 8: y_stray_warp_kernel<T, NOUT, 8><<<nb, nt, smem, st>>>(d, w, pg); break;
-        default: y_stray_warp_kernel<T, NOUT, 16><<<nb, nt, smem, st>>>(d, w, pg); break;
+        case 2: launch_pdl(y_stray_warp_kernel<T, NOUT, 2>, nb, nt, smem, st, d, w, pg); break;
+        case 4: launch_pdl(y_stray_warp_kernel<T, NOUT, 4>, nb, nt, smem, st, d, w, pg); break;
+        case 8: launch_pdl(y_stray_warp_kernel<T, NOUT, 8>, nb, nt, smem, st, d, w, pg); break;
+        default: launch_pdl(y_stray_warp_kernel<T, NOUT, 16>, nb, nt, smem, st, d, w, pg); break;
     }
 }
 template <typename T>

@@ -128,6 +128,12 @@ struct Dev {
     const long long* step_ctr;
 };
 
+// ---- programmatic dependent launch ------------------------------------------------------------
+// Every pass kernel lets the next launch start at once; that launch runs its set-up (work item,
+// film record, twiddle staging: data no kernel writes) and then waits for this grid to finish.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- error-free transformations (FP32 double-float arithmetic of the state) -----------------
 // Knuth's two-sum, Dekker's fast two-sum and the FMA two-product.
 template <typename T> __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {

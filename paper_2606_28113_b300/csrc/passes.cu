@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PHASE_MARK(14);
+    pdl_launch_dependents();
     const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
     const int y = wi.y;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     if (Lo.dt)
         for (int i = threadIdx.x; i < 2 * nz * nz; i += blockDim.x) sdt[i] = d.dtab[F.gdtab_z + i];
     __syncthreads();
+    pdl_wait();   // everything above reads constant data; fields of the previous pass from here on
     const int S = Lo.slab;
     const int KC = Lo.kc;
     const int npx = (nz + 1) / 2;
@@ -533,6 +535,7 @@ template <typename T, int NY>
 __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_launch_dependents();
     const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
     const int kz = wi.y, kx0 = wi.z, tn = wi.w;
@@ -545,6 +548,7 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
         stw[ny + i] = d.tw[F.gtw4_dy + i];
     }
     __syncthreads();
+    pdl_wait();
     const int npair = (tn + 1) / 2;
     V* c0 = stw + 2 * ny;
     V* c1 = c0 + npair * ny;
@@ -742,6 +746,7 @@ template <typename T, int NOUT, int E>
 __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_launch_dependents();
     const int4 wi = work[blockIdx.x];
     const Film& F = d.films[wi.x];
     const int kz = wi.y, kx0 = wi.z, tn = wi.w;
@@ -752,6 +757,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     V* stw = reinterpret_cast<V*>(smem_raw);
     stage_plan<T>(ppy, d.tw, stw, 0, false);
     __syncthreads();
+    pdl_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= tn) return;
     V* scr = stw + Py + warp * Py;
