@@ -66,6 +66,8 @@ struct sgspm_ctx {
     void* d_field[kMaxSlots] = {};
     void* d_flo[kMaxSlots] = {};       // low parts of the double-float state slots (FP32 form)
     void* d_spec[kMaxSpec] = {};
+    void* d_ycache = nullptr;          // y transforms of M_1..3 for the register stray pass
+    long long nycache = 0;             // complex elements per component
     void** d_tab = nullptr;            // device copies of the three pointer tables
     void** d_tab_lo = nullptr;
     void** d_tab_spec = nullptr;
@@ -194,6 +196,8 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
     d.flo = (T* const*)ctx->d_tab_lo;
     d.spec = (cplx<T>* const*)ctx->d_tab_spec;
     d.he_cell = ctx->he_cell ? (const T*)ctx->d_he : nullptr;
+    d.ycache = (cplx<T>*)ctx->d_ycache;
+    d.ycache_n = ctx->nycache;
     d.status = ctx->d_status;
     d.step_ctr = ctx->d_step;
     return d;
@@ -266,8 +270,9 @@ static cudaError_t attr_yh(int key, size_t smem) {
 }
 // key = E = Py / 32
 template <typename T, int NOUT>
-static void launch_yw_n(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
+static void launch_yw_n(int key, int nb, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
     const unsigned nt = 32 * kWarpLines;
+    const size_t smem = yw_smem_bytes<T>(32 * key, NOUT);
     switch (key) {
         case 2: launch_pdl(y_stray_warp_kernel<T, NOUT, 2>, nb, nt, smem, st, d, w, pg); break;
         case 4: launch_pdl(y_stray_warp_kernel<T, NOUT, 4>, nb, nt, smem, st, d, w, pg); break;
@@ -276,10 +281,10 @@ static void launch_yw_n(int key, int nb, size_t smem, cudaStream_t st, const Dev
     }
 }
 template <typename T>
-static void launch_yw(int key, int nout, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
-    if (nout == 1) launch_yw_n<T, 1>(key, nb, smem, st, d, w, pg);
-    else if (nout == 2) launch_yw_n<T, 2>(key, nb, smem, st, d, w, pg);
-    else launch_yw_n<T, 3>(key, nb, smem, st, d, w, pg);
+static void launch_yw(int key, int nout, int nb, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
+    if (nout == 1) launch_yw_n<T, 1>(key, nb, st, d, w, pg);
+    else if (nout == 2) launch_yw_n<T, 2>(key, nb, st, d, w, pg);
+    else launch_yw_n<T, 3>(key, nb, st, d, w, pg);
 }
 template <typename T, int NOUT>
 static cudaError_t attr_yw_n(int key, size_t smem) {
@@ -304,7 +309,7 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
         case 2: {
             int n = L.y.n;
             if (ctx->warp_stray) {
-                for (const auto& c : ctx->yw_cls) launch_yw<T>(c.key, n, c.n, c.smem, st, d, c.work, L.y);
+                for (const auto& c : ctx->yw_cls) launch_yw<T>(c.key, n, c.n, st, d, c.work, L.y);
             } else {
                 y_stray_kernel<T><<<ctx->n_ys[n], kThreads, ctx->smem_ys[n], st>>>(d, ctx->d_work_ys[n], L.y, ctx->tx_s[n]);
             }
@@ -362,13 +367,18 @@ static XZProg xz_empty() {
     return p;
 }
 
-static Launch mk_ystray(const std::vector<int>& outs) {
+// fresh: components whose x,z spectrum changed since the cache was written (transformed along
+// y, and stored when in `store`); the others are read from the y-transform cache.  The cache is
+// only used by the register stray pass; the fallback pass always transforms all three.
+static Launch mk_ystray(const std::vector<int>& outs, int fresh = 7, int store = 0) {
     Launch L;
     memset(&L, 0, sizeof(L));
     L.kind = 2;
     L.y.kind = 1;
     L.y.n = (int)outs.size();
     L.y.in_mask = 7;
+    L.y.fresh_mask = fresh;
+    L.y.store_mask = store;
     for (int i = 0; i < 3; ++i) L.y.in_spec[i] = S1 + i;
     for (size_t o = 0; o < outs.size(); ++o) {
         L.y.slot[o] = outs[o];
@@ -463,7 +473,11 @@ static void build_record(sgspm_ctx* ctx) {
     const bool st = ctx->stray;
     std::vector<Launch>& P = ctx->rec_prog;
     P.clear();
-    if (st) P.push_back(mk_ystray({1, 2}));
+    const bool yc = st && ctx->warp_stray;
+    auto ys = [&](const std::vector<int>& outs, int fresh, int store) {
+        return yc ? mk_ystray(outs, fresh, store) : mk_ystray(outs);
+    };
+    if (st) P.push_back(ys({1, 2}, 7, 7));
     P.push_back(mk_rhs(ctx, {1, 2}, M1, M2, M3, 0));
     P.push_back(mk_yheat({1, 2}, 0));
     {
@@ -475,23 +489,23 @@ static void build_record(sgspm_ctx* ctx) {
         L.xz.inv_store[1] = E3N;
         P.push_back(L);
     }
-    if (st) P.push_back(mk_ystray({0}));
+    if (st) P.push_back(ys({0}, 1, 1));
     P.push_back(mk_rhs(ctx, {0}, A1, M2, M3, 0));
     P.push_back(mk_yheat({0}, 0));
     P.push_back(mk_gs(ctx, 0, E1S, A2, M2, E3N, A1, slab(0), M3, 1));
-    if (st) P.push_back(mk_ystray({1}));
+    if (st) P.push_back(ys({1}, 2, 2));
     P.push_back(mk_rhs(ctx, {1}, A1, A2, M3, 0));
     P.push_back(mk_yheat({1}, 0));
     P.push_back(mk_gs(ctx, 1, D2S, A3, M3, E1S, A2, slab(0), A1, 2));
-    if (st) P.push_back(mk_ystray({2}));
+    if (st) P.push_back(ys({2}, 4, 4));
     P.push_back(mk_rhs(ctx, {2}, A1, A2, A3, 0));
     P.push_back(mk_yheat({2}, 0));
     P.push_back(mk_gs(ctx, 2, E3SS, B2, M2, slab(0), A1, E1S, A3, 1));
-    if (st) P.push_back(mk_ystray({1}));
+    if (st) P.push_back(ys({1}, 2, 2));
     P.push_back(mk_rhs(ctx, {1}, A1, B2, A3, 0));
     P.push_back(mk_yheat({1}, 0));
     P.push_back(mk_gs(ctx, 1, D2SS, B1, M1, slab(0), A3, E3SS, B2, 0));
-    if (st) P.push_back(mk_ystray({0, 1, 2}));
+    if (st) P.push_back(ys({0, 1, 2}, 1, 0));
     {
         Launch L = mk_rhs(ctx, {0, 1, 2}, B1, B2, A3, 1);
         if (st)
@@ -680,7 +694,11 @@ static void build_programs(sgspm_ctx* ctx) {
     P.clear();
     // components: 0 = paper's m1, 1 = m2, 2 = m3.  delta_i = g_i - m_i (see DESIGN: delta form)
     // h_s at m^n, then g2^n, g3^n
-    if (st) P.push_back(mk_ystray(R2 ? std::vector<int>{0, 1, 2} : std::vector<int>{1, 2}));
+    const bool yc = st && !R2 && ctx->warp_stray;   // y-transform cache: refresh only what changed
+    auto cached = [&](const std::vector<int>& outs, int fresh, int store) {
+        return yc ? mk_ystray(outs, fresh, store) : mk_ystray(outs);
+    };
+    if (st) P.push_back(R2 ? mk_ystray({0, 1, 2}) : cached({1, 2}, 7, 7));
     P.push_back(mk_rhs(ctx, {1, 2}, M1, M2, M3, 0));
     P.push_back(mk_yheat({1, 2}, 0));
     {
@@ -694,7 +712,7 @@ static void build_programs(sgspm_ctx* ctx) {
         P.push_back(L);
     }
     auto refresh = [&](int comp) {
-        if (st && !R2) P.push_back(mk_ystray({comp}));
+        if (st && !R2) P.push_back(cached({comp}, 1 << comp, 1 << comp));
     };
     // g1* at (m1*, m2, m3) -> m2* = m2 + d3n m1* - d1* m3
     refresh(0);
@@ -747,8 +765,9 @@ static void build_programs(sgspm_ctx* ctx) {
         }
         P.push_back(L);
     }
-    // Step 2: damping heat flow at m**, Step 3: projection
-    if (st) P.push_back(mk_ystray({0, 1, 2}));
+    // Step 2: damping heat flow at m**, Step 3: projection (only the component the last
+    // Gauss-Seidel update changed is new: m1 for SGSPM, m3 for GSPM)
+    if (st) P.push_back(R2 ? mk_ystray({0, 1, 2}) : cached({0, 1, 2}, gspm ? 4 : 1, 0));
     P.push_back(mk_rhs(ctx, {0, 1, 2}, m1f, m2f, m3f, 1));
     P.push_back(mk_yheat({0, 1, 2}, 1));
     P.push_back(mk_final(ctx, m1f, m2f, m3f));
@@ -956,7 +975,7 @@ static int newell_setup(sgspm_ctx* ctx, const Film& F) {
         newell_axis_kernel<<<(unsigned)((nC + 255) / 256), 256>>>(B, C, 2, nz, Hz, F.Pz, Hy * Kx, 1, (long long)Hy * Kx, 1, 0,
                                                                  (long long)nz * Hy * Kx, (long long)Hy * Kx, 1, 0,
                                                                  (long long)Hz * Hy * Kx, cs(2), sn(2));
-        newell_finish_kernel<T><<<(unsigned)((nC + 255) / 256), 256>>>(C, (T*)ctx->d_ktab + F.off_ktab, Kx, Hy, Hz,
+        newell_finish_kernel<T><<<(unsigned)((nC + 255) / 256), 256>>>(C, (T*)ctx->d_ktab + F.off_ktab, Kx, Hy, ktab_row(F.Py), Hz,
                                                                        1.0 / ((double)F.Px * F.Py * F.Pz));
         e = cudaGetLastError();
     }
@@ -977,7 +996,7 @@ static int setup_t(sgspm_ctx* ctx) {
     std::vector<double> lam;
     ctx->dtab_host.clear();
     // plans, offsets
-    long long oc = 0, os = 0, ok = 0;
+    long long oc = 0, os = 0, ok = 0, oyc = 0;
     std::map<std::vector<double>, long long> ktab_of;
     std::vector<int> ktab_owner;   // film that computes each unique table (or -1)
     for (int f = 0; f < ctx->nfilm; ++f) {
@@ -1029,6 +1048,8 @@ static int setup_t(sgspm_ctx* ctx) {
         oc += (long long)F.nx * F.ny * F.nz;
         F.off_spec = os;
         os += (long long)F.Kx * F.ny * F.Pz;
+        F.off_ycache = oyc;
+        oyc += (long long)F.Pz * F.Kx * F.Py;
         F.lam = (int)lam.size();
         const int ns[3] = {F.nx, F.ny, F.nz};
         const double hs[3] = {F.hx, F.hy, F.hz};
@@ -1044,7 +1065,7 @@ static int setup_t(sgspm_ctx* ctx) {
             if (it == ktab_of.end()) {
                 F.off_ktab = ok;
                 ktab_of[key] = ok;
-                ok += 6LL * (F.Pz / 2 + 1) * (F.Py / 2 + 1) * F.Kx;
+                ok += 6LL * (F.Pz / 2 + 1) * ktab_row(F.Py) * F.Kx;
                 ktab_owner.push_back(f);
             } else {
                 F.off_ktab = it->second;
@@ -1053,6 +1074,7 @@ static int setup_t(sgspm_ctx* ctx) {
     }
     ctx->ncell = oc;
     ctx->nspec = os;
+    ctx->nycache = oyc;
     ctx->nktab = ok;
     // shared-memory budgets
     int dev = 0;
@@ -1141,7 +1163,8 @@ static int setup_t(sgspm_ctx* ctx) {
     // register-resident stray pass when every film's padded y length is 64..512, per length class
     ctx->warp_stray = ctx->stray;
     for (const Film& F : ctx->films)
-        if (!(F.Py == 64 || F.Py == 128 || F.Py == 256 || F.Py == 512)) ctx->warp_stray = false;
+        if (!(F.Py == 64 || F.Py == 128 || F.Py == 256 || F.Py == 512) || yw_smem_bytes<T>(F.Py, 3) > (size_t)smem_max)
+            ctx->warp_stray = false;
     if (ctx->warp_stray) {
         std::map<int, std::vector<int4>> ws;
         for (int f = 0; f < ctx->nfilm; ++f) {
@@ -1151,10 +1174,12 @@ static int setup_t(sgspm_ctx* ctx) {
                     ws[F.Py / 32].push_back(make_int4(f, kz, x0, std::min(kWarpLines, F.Kx - x0)));
         }
         for (auto& kv : ws) {
-            const size_t smem = (size_t)(1 + kWarpLines) * 32 * kv.first * V;
-            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), smem};
+            const int Py = 32 * kv.first;
+            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), yw_smem_bytes<T>(Py, 3)};
             if ((rc = up4(&c.work, kv.second))) return rc;
-            cudaError_t e1 = attr_yw_n<T, 1>(c.key, smem), e2 = attr_yw_n<T, 2>(c.key, smem), e3 = attr_yw_n<T, 3>(c.key, smem);
+            cudaError_t e1 = attr_yw_n<T, 1>(c.key, yw_smem_bytes<T>(Py, 1));
+            cudaError_t e2 = attr_yw_n<T, 2>(c.key, yw_smem_bytes<T>(Py, 2));
+            cudaError_t e3 = attr_yw_n<T, 3>(c.key, yw_smem_bytes<T>(Py, 3));
             CK(e1);
             CK(e2);
             CK(e3);
@@ -1193,6 +1218,11 @@ static int setup_t(sgspm_ctx* ctx) {
             CK(cudaMemset(ctx->d_spec[i], 0, (size_t)ctx->nspec * V));
         }
         CK(cudaMalloc(&ctx->d_ktab, (size_t)ctx->nktab * sizeof(T)));
+        CK(cudaMemset(ctx->d_ktab, 0, (size_t)ctx->nktab * sizeof(T)));   // line padding stays zero
+        if (ctx->warp_stray) {
+            CK(cudaMalloc(&ctx->d_ycache, (size_t)(3 * ctx->nycache) * sizeof(cplx<T>)));
+            CK(cudaMemset(ctx->d_ycache, 0, (size_t)(3 * ctx->nycache) * sizeof(cplx<T>)));
+        }
         for (int f : ktab_owner)
             if ((rc = newell_setup<T>(ctx, ctx->films[f]))) return rc;
     }
@@ -1223,7 +1253,7 @@ static void release(sgspm_ctx* ctx) {
     for (int i = 0; i < kMaxSpec; ++i)
         if (ctx->d_spec[i]) cudaFree(ctx->d_spec[i]);
     void* more[] = {ctx->d_tab, ctx->d_tab_lo, ctx->d_tab_spec, ctx->d_ckpt, ctx->d_seg, ctx->d_final, ctx->d_apart,
-                    ctx->d_alpha_b};
+                    ctx->d_alpha_b, ctx->d_ycache};
     for (void* p : more)
         if (p) cudaFree(p);
     for (int n = 0; n < 4; ++n)

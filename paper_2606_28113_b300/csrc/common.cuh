@@ -44,6 +44,7 @@ struct Film {
     int pad_;
     long long off_cell;      // offset into every real field pool
     long long off_spec;      // offset into every spectral pool: Kx * ny * Pz per film
+    long long off_ycache;    // offset into the y-transform cache: Pz * Kx * Py per film
     long long off_ktab;      // kernel-table offset: 6 * (Pz/2+1) * (Py/2+1) * Kx
     int lam;                 // offset of lambda_x[nx], lambda_y[ny], lambda_z[nz] in the eigen pool
     int plan_dx, plan_dy, plan_dz;   // DCT lengths nx, ny, nz
@@ -102,6 +103,8 @@ struct YProg {
     int in_spec[3];        // stray: spectral slots of M_1, M_2, M_3
     int in_mask;           // stray: bit b set if input component b is non-zero (others skipped)
     int out_spec[3];       // stray: spectral slot of H_a for each output
+    int fresh_mask;        // stray: bit b set: transform M_b along y (else read its cached transform)
+    int store_mask;        // stray: bit b set: store the new y transform of M_b in the cache
 };
 
 // Gauss-Legendre rules on [-1, 1] used by the Newell set-up, packed: order q at off[q].
@@ -124,6 +127,8 @@ struct Dev {
     T* const* flo;         // device table: low parts of double-float state slots (FP32 form), else null
     cplx<T>* const* spec;  // device table: spectral slot -> pool pointer
     const T* he_cell;      // per-cell applied field [3][ncell_total] or null
+    cplx<T>* ycache;       // y transforms of M_1..3 (register order), component stride ycache_n
+    long long ycache_n;
     int* status;
     const long long* step_ctr;
 };
@@ -133,6 +138,29 @@ struct Dev {
 // film record, twiddle staging: data no kernel writes) and then waits for this grid to finish.
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ---- asynchronous global -> shared copies (cp.async; completion per thread by commit group) ----
+__device__ __forceinline__ void cp_async_8(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
+    static_assert(BYTES == 8 || BYTES == 16, "cp.async piece of 8 or 16 bytes");
+    if constexpr (BYTES == 8) cp_async_8(sdst, gsrc);
+    else cp_async_16(sdst, gsrc);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most `pending` (0, 1 or 2) of this thread's committed groups are still in flight
+__device__ __forceinline__ void cp_async_wait(int pending) {
+    if (pending >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
 
 // ---- error-free transformations (FP32 double-float arithmetic of the state) -----------------
 // Knuth's two-sum, Dekker's fast two-sum and the FMA two-product.

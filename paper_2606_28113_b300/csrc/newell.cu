@@ -161,7 +161,8 @@ __global__ void newell_axis_kernel(const double* __restrict__ in, double* __rest
 // ktab[c][kz][kx][ky] = -(+-) N_hat / (Px Py Pz) from nhat[c][kz][ky][kx]: the two odd axes
 // of an off-diagonal component contribute (-i)^2 = -1.
 template <typename T>
-__global__ void newell_finish_kernel(const double* __restrict__ nhat, T* __restrict__ ktab, int Kx, int Hy, int Hz, double scale) {
+__global__ void newell_finish_kernel(const double* __restrict__ nhat, T* __restrict__ ktab, int Kx, int Hy, int HyP, int Hz,
+                                     double scale) {
     long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long n6 = (long long)Hz * Hy * Kx;
     if (id >= 6 * n6) return;
@@ -173,7 +174,7 @@ __global__ void newell_finish_kernel(const double* __restrict__ nhat, T* __restr
     const int kz = (int)(r / Hy);
     double v = nhat[id];
     if (c >= 3) v = -v;
-    ktab[ktab_index(c, kx, kz, ky, Kx, Hy, Hz)] = (T)(-v * scale);
+    ktab[ktab_index(c, kx, kz, ky, Kx, HyP, Hz)] = (T)(-v * scale);
 }
 
 }  // namespace sgspm

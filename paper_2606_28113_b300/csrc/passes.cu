@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
     V* w0 = stw + Py;
     V* w1 = w0 + B;
     V* acc = w1 + B;     // pg.n accumulators
-    const int Hy = Py / 2 + 1, Hz = Pz / 2 + 1;
+    const int HyP = ktab_row(Py), Hz = Pz / 2 + 1;
     const int kzr = kz <= Pz - kz ? kz : Pz - kz;
     const bool zodd = kz > Pz / 2;
     const T* kt = d.ktab + F.off_ktab;
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
                     for (int o = 0; o < 3; ++o) {
                         if (o < pg.n) {
                             const int cc = pair_idx(pg.slot[o], b);
-                            T k = kt[ktab_index(cc, kx0 + t, kzr, kyr, Kx, Hy, Hz)];
+                            T k = kt[ktab_index(cc, kx0 + t, kzr, kyr, Kx, HyP, Hz)];
                             const bool neg = ((cc == 3 || cc == 5) && yodd) != ((cc == 4 || cc == 5) && zodd);
                             kv[u][o] = neg ? -k : k;
                         }
@@ -679,19 +679,67 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
 }
 
 // Register-resident stray-field line pass: one warp per kx line (Py = 32 E, E in {2,4,8,16}).
-// For each input component b: load the x,z spectrum line (y < ny, zero padded), forward FFT in
-// registers, multiply-accumulate with the Newell table in the FFT's own output order; then the
-// adjoint FFT of each output and a store of y < ny.  No block barrier after the twiddle staging.
+// The CTA first issues asynchronous copies of everything it reads: for each input component b
+// the (y < ny, kx0..kx0+lines) tile of the x,z spectrum (fresh components only) and the Newell
+// table lines of the pairs (out, b), one commit group per component, so that all loads are in
+// flight together.  Then, per component: forward FFT in registers (zero padded) of a fresh
+// component, optionally stored to the y-transform cache in register order, or the cached
+// transform of an unchanged one; multiply-accumulate with the table in the FFT's own output
+// order.  Finally the adjoint FFT of each output and a store of y < ny.  Within one step the
+// Gauss-Seidel sweep changes one component between refreshes, so a refresh transforms one
+// input instead of three.
 template <typename T, int NOUT, int E>
-__device__ __forceinline__ void y_stray_line(const Dev<T>& d, const Film& F, const YProg& pg, int kz, int kx,
-                                             cplx<T>* scr, const cplx<T>* tw, int lane) {
+__global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
-    const int ny = F.ny, Kx = F.Kx, Pz = F.Pz;
-    const int Hy = P / 2 + 1, Hz = Pz / 2 + 1;
+    constexpr int LI = P / 2 + 8;                 // yw_line_stride
+    constexpr int HyP = ((P / 2 + 1) + 3) & ~3;   // ktab_row
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_launch_dependents();
+    const int4 wi = work[blockIdx.x];
+    const Film& F = d.films[wi.x];
+    const int kz = wi.y, kx0 = wi.z, tn = wi.w;
+    const int ny = F.ny, Kx = F.Kx, Pz = F.Pz, Hz = Pz / 2 + 1;
     const int kzr = kz <= Pz - kz ? kz : Pz - kz;
     const bool zodd = kz > Pz / 2;
+    V* stw = reinterpret_cast<V*>(smem_raw);
+    V* scr0 = stw + P;
+    V* inb = scr0 + kWarpLines * P;                                       // [3][lines][LI]
+    T* kbuf = reinterpret_cast<T*>(inb + 3 * kWarpLines * LI);            // [3 NOUT][lines][HyP]
+    {
+        const V* g = d.tw + d.plans[F.plan_py].tw;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = g[i];
+    }
+    pdl_wait();
+    // ---- asynchronous staging: group b = input component b and the table lines of (o, b)
+    const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx0;
     const T* kt = d.ktab + F.off_ktab;
+    constexpr int KCH = 16 / (int)sizeof(T);   // table elements per 16-byte piece
+    const int nkch = tn * HyP / KCH;
+#pragma unroll 1
+    for (int b = 0; b < 3; ++b) {
+        if (pg.in_mask & (1 << b)) {
+            const V* Sb = d.spec[pg.in_spec[b]] + line0;
+            const bool fresh = (pg.fresh_mask >> b) & 1;
+            V* dst = inb + b * kWarpLines * LI;
+            const int n = fresh ? tn * ny : 0;
+            for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+                const int y = idx / tn, t = idx - y * tn;
+                cp_async<(int)sizeof(V)>(dst + t * LI + y, Sb + (long long)y * Kx + t);
+            }
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                const int cc = pair_idx(pg.slot[o], b);
+                const T* src = kt + (((long long)cc * Hz + kzr) * Kx + kx0) * HyP;
+                T* kd = kbuf + (o * 3 + b) * kWarpLines * HyP;
+                for (int i = threadIdx.x; i < nkch; i += blockDim.x) cp_async_16(kd + i * KCH, src + i * KCH);
+            }
+        }
+        cp_async_commit();
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool active = warp < tn;
+    V* scr = scr0 + warp * P;
     const int q = lane / G, g = lane % G;
     const int s2 = bitrev_lanes(g, G);
     V acc[NOUT][E];
@@ -699,24 +747,37 @@ __device__ __forceinline__ void y_stray_line(const Dev<T>& d, const Film& F, con
     for (int o = 0; o < NOUT; ++o)
 #pragma unroll
         for (int s1 = 0; s1 < E; ++s1) acc[o][s1] = cmk<V>(T(0), T(0));
-    const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx;
+    // cached y transforms: line (kz, kx) of component b, element s1 * 32 + lane = register v[s1]
+    const long long cline = F.off_ycache + ((long long)kz * Kx + kx0 + warp) * P + lane;
 #pragma unroll 1
     for (int b = 0; b < 3; ++b) {
-        if (!(pg.in_mask & (1 << b))) continue;
-        const V* Sb = d.spec[pg.in_spec[b]] + line0;
+        cp_async_wait(2 - b);
+        __syncthreads();
+        if (!active || !(pg.in_mask & (1 << b))) continue;
         V v[E];
+        V* cb = d.ycache + b * d.ycache_n + cline;
+        if ((pg.fresh_mask >> b) & 1) {
+            const V* line = inb + (b * kWarpLines + warp) * LI;
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int y = lane + 32 * k;
-            v[k] = y < ny ? Sb[(long long)y * Kx] : cmk<V>(T(0), T(0));
+            for (int k = 0; k < E; ++k) {
+                const int y = lane + 32 * k;
+                v[k] = y < ny ? line[y] : cmk<V>(T(0), T(0));
+            }
+            wreg_fwd<T, E>(v, scr, stw, lane);
+            if ((pg.store_mask >> b) & 1) {
+#pragma unroll
+                for (int s1 = 0; s1 < E; ++s1) cb[s1 * 32] = v[s1];
+            }
+        } else {
+#pragma unroll
+            for (int s1 = 0; s1 < E; ++s1) v[s1] = cb[s1 * 32];
         }
-        wreg_fwd<T, E>(v, scr, tw, lane);
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) {
             const int cc = pair_idx(pg.slot[o], b);
             const bool yflip = (cc == 3 || cc == 5);
             const bool zflip = (cc == 4 || cc == 5) && zodd;
-            const T* kb = kt + (((long long)cc * Hz + kzr) * Kx + kx) * Hy;
+            const T* kb = kbuf + ((o * 3 + b) * kWarpLines + warp) * HyP;
 #pragma unroll
             for (int s1 = 0; s1 < E; ++s1) {
                 const int ky = q + E * (s1 + E * s2);
@@ -728,41 +789,18 @@ __device__ __forceinline__ void y_stray_line(const Dev<T>& d, const Film& F, con
             }
         }
     }
+    if (!active) return;
+    const long long out0 = line0 + warp;
 #pragma unroll
     for (int o = 0; o < NOUT; ++o) {
-        wreg_adj<T, E>(acc[o], scr, tw, lane);
-        V* Ho = d.spec[pg.out_spec[o]] + line0;
+        wreg_adj<T, E>(acc[o], scr, stw, lane);
+        V* Ho = d.spec[pg.out_spec[o]] + out0;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             const int y = lane + 32 * k;
             if (y < ny) Ho[(long long)y * Kx] = acc[o][k];
         }
     }
-}
-
-constexpr int kWarpLines = 4;   // kx lines (warps) per CTA of the register stray pass
-
-template <typename T, int NOUT, int E>
-__global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
-    using V = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_launch_dependents();
-    const int4 wi = work[blockIdx.x];
-    const Film& F = d.films[wi.x];
-    const int kz = wi.y, kx0 = wi.z, tn = wi.w;
-    const int Py = F.Py;
-    __shared__ Plan ppy;
-    if (threadIdx.x == 0) ppy = d.plans[F.plan_py];
-    __syncthreads();
-    V* stw = reinterpret_cast<V*>(smem_raw);
-    stage_plan<T>(ppy, d.tw, stw, 0, false);
-    __syncthreads();
-    pdl_wait();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp >= tn) return;
-    V* scr = stw + Py + warp * Py;
-    const int kx = kx0 + warp;
-    y_stray_line<T, NOUT, E>(d, F, pg, kz, kx, scr, stw, lane);
 }
 
 // ------------------------------------------------------------------------------------------

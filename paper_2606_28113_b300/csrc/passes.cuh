@@ -58,9 +58,27 @@ __device__ __forceinline__ void stage_plan(Plan& pl, const cplx<T>* __restrict__
         for (int i = threadIdx.x; i < P; i += blockDim.x) stw[off + P + i] = g[pl.tw4 + i];
 }
 
-// Newell table layout [c][kz'][kx][ky'] (ky' fastest: a y line reads it contiguously)
-__host__ __device__ inline long long ktab_index(int c, int kx, int kzr, int kyr, int Kx, int Hy, int Hz) {
-    return (((long long)c * Hz + kzr) * Kx + kx) * Hy + kyr;
+// Newell table layout [c][kz'][kx][ky'] (ky' fastest: a y line reads it contiguously).  A line
+// holds Py/2 + 1 values and is padded to a multiple of 4 elements (HyP), so that every line
+// starts on a 16-byte boundary and can be copied to shared memory in 16-byte pieces.
+__host__ __device__ inline int ktab_row(int Py) { return ((Py / 2 + 1) + 3) & ~3; }
+
+__host__ __device__ inline long long ktab_index(int c, int kx, int kzr, int kyr, int Kx, int HyP, int Hz) {
+    return (((long long)c * Hz + kzr) * Kx + kx) * HyP + kyr;
+}
+
+// Register stray pass (one warp per kx line, Py = 32 E): shared-memory layout of one CTA of
+// kWarpLines lines.  Complex: [W_Py | scratch per warp (Py) | staged input lines 3 x lines x LI];
+// real: staged table lines [3 NOUT][lines][HyP].  LI = Py/2 + 8 makes the asynchronous copies of
+// a (y, kx) tile land two lanes per bank (the minimum for 8-byte elements).
+constexpr int kWarpLines = 4;   // kx lines (warps) per CTA of the register stray pass
+
+__host__ __device__ inline int yw_line_stride(int Py) { return Py / 2 + 8; }
+
+template <typename T>
+__host__ __device__ inline size_t yw_smem_bytes(int Py, int nout) {
+    return (size_t)(Py + kWarpLines * Py + 3 * kWarpLines * yw_line_stride(Py)) * sizeof(cplx<T>) +
+           (size_t)3 * nout * kWarpLines * ktab_row(Py) * sizeof(T);
 }
 
 }  // namespace sgspm
