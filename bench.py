@@ -13,6 +13,10 @@ Default arm: the CUDA library through its C ABI.  Every timed step starts with a
 rank advances its own replica film (replicas only: a film does not shard), so the
 whole-job value is the sum over ranks of cells x steps / max-over-ranks time.
 
+Beside the line, "ensemble" reports the batched workload: 256 films of four sizes (64x64x2,
+96x64x2, 128x128x4, 128x64x4; per-film alpha and applied field) stepped together in one
+handle, FP32 form, aggregate cell-steps/s (--ensemble-steps, 0 to skip).
+
 --impl reference: the FP64 CPU oracle (oracle/) on the host cores, same film and metric,
 each step one full oracle step; rank 0 only.
 """
@@ -165,6 +169,35 @@ def algorithmic_bytes_per_cell(kind, ncomp=1):
     return None
 
 
+def run_ensemble(sgspm, torch, stream, steps, warmup=3):
+    """Aggregate throughput of the batched workload: 256 films of four sizes in one handle (FP32)."""
+    films = inputs.ensemble(seed=0, nfilm=256)
+    m0 = np.concatenate([inputs.random_unit(f["seed"], f["n"]).reshape(-1) for f in films])
+    H = sgspm.Handle(films, fp64=False, stream=stream.cuda_stream)
+    H.set_m(torch.from_numpy(m0.astype(np.float32)).cuda())
+    H.step(warmup)
+    H.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    H.step(steps)
+    b.record(stream)
+    H.sync()
+    ms = a.elapsed_time(b)
+    lps = H.launches_per_step()
+    prof = {}
+    for kind, t in H.profile_step():
+        prof[kind] = prof.get(kind, 0.0) + t
+    tot = sum(prof.values())
+    H.close()
+    ncell = sum(int(np.prod(f["n"])) for f in films)
+    sizes = " | ".join("x".join(map(str, n)) for n in inputs.ENSEMBLE_SIZES)
+    return {"workload": f"ensemble256 ({sizes}; per-film alpha, h_e)", "films": len(films), "cells": ncell,
+            "value": ncell * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup, "dtype": "f32", "l2": "working set larger than L2 (no flush)",
+            "launches_per_step": lps, "launch_shares": {str(k): v / tot for k, v in sorted(prof.items())}}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as tdist
@@ -281,6 +314,7 @@ def run_gpu(args):
     e2e_val = world * ncell * ne / e2e_s
     launches = args.steps * H.launches_per_step()
     H.close()
+    ens = run_ensemble(sgspm, torch, stream, args.ensemble_steps) if args.ensemble_steps > 0 else None
 
     if rank == 0:
         cpu, _ = cpu_baseline(w, m0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else (None, None)
@@ -301,6 +335,7 @@ def run_gpu(args):
                         "d2h_bytes_per_step": 3 * ncell * 4,
                         "path": "sgspm_set_field(pinned host f32) + sgspm_step(1) + sgspm_get_field(pinned host f32)"},
                 "gpu_launches": launches,
+                "ensemble": ens,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -314,6 +349,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps for cpu_baseline (0: skip)")
+    ap.add_argument("--ensemble-steps", type=int, default=20,
+                    help="timed steps of the 256-film batched workload, reported beside the line (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
