@@ -15,7 +15,8 @@ whole-job value is the sum over ranks of cells x steps / max-over-ranks time.
 
 Beside the line, "ensemble" reports the batched workload: 256 films of four sizes (64x64x2,
 96x64x2, 128x128x4, 128x64x4; per-film alpha and applied field) stepped together in one
-handle, FP32 form, aggregate cell-steps/s (--ensemble-steps, 0 to skip).
+handle, FP32 form, aggregate cell-steps/s (--ensemble-steps, 0 to skip); "strip" the
+512x64x4 Neel-wall strip (cell-steps/s and the wall's displacement; --strip-steps).
 
 --impl reference: the FP64 CPU oracle (oracle/) on the host cores, same film and metric,
 each step one full oracle step; rank 0 only.
@@ -198,6 +199,37 @@ def run_ensemble(sgspm, torch, stream, steps, warmup=3):
             "launches_per_step": lps, "launch_shares": {str(k): v / tot for k, v in sorted(prof.items())}}
 
 
+def run_strip(sgspm, torch, stream, steps):
+    """The 512x64x4 strip with a Neel wall (h = 0.1, Q = 0.1, h_e = 0.005 along +x, alpha = 1e-2,
+    dt = 0.005), FP32 form: cell-steps/s and the wall's displacement (zero of <m_x>(x), cells)."""
+    w = dict(inputs.WORKLOADS["strip512x64x4_wall"], alpha=1e-2)
+    m0 = inputs.initial_state(w)
+    H = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
+                   stream=stream.cuda_stream)
+    H.set_m(m0)
+    H.step(3)
+    H.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    H.step(steps)
+    b.record(stream)
+    H.sync()
+    ms = a.elapsed_time(b)
+
+    def wall(m):
+        mx = m[0].mean(axis=(0, 1))
+        i = int(np.nonzero(np.sign(mx[:-1]) != np.sign(mx[1:]))[0][0])
+        return i + 0.5 + mx[i] / (mx[i] - mx[i + 1])
+
+    x1 = wall(H.split(H.get_m())[0])
+    H.close()
+    ncell = int(np.prod(w["n"]))
+    return {"workload": "strip512x64x4_wall (Neel wall, alpha 1e-2)", "cells": ncell, "dtype": "f32",
+            "value": ncell * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "wall_displacement_cells": x1 - wall(m0), "after_steps": steps + 3,
+            "l2": "not flushed (working set in L2)"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as tdist
@@ -315,6 +347,7 @@ def run_gpu(args):
     launches = args.steps * H.launches_per_step()
     H.close()
     ens = run_ensemble(sgspm, torch, stream, args.ensemble_steps) if args.ensemble_steps > 0 else None
+    strip = run_strip(sgspm, torch, stream, args.strip_steps) if args.strip_steps > 0 else None
 
     if rank == 0:
         cpu, _ = cpu_baseline(w, m0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else (None, None)
@@ -336,6 +369,7 @@ def run_gpu(args):
                         "path": "sgspm_set_field(pinned host f32) + sgspm_step(1) + sgspm_get_field(pinned host f32)"},
                 "gpu_launches": launches,
                 "ensemble": ens,
+                "strip": strip,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -349,6 +383,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps for cpu_baseline (0: skip)")
+    ap.add_argument("--strip-steps", type=int, default=400,
+                    help="timed steps of the 512x64x4 Neel-wall strip, reported beside the line (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed steps of the 256-film batched workload, reported beside the line (0: skip)")
     args = ap.parse_args()

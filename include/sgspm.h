@@ -108,6 +108,10 @@ int sgspm_create_batch(int nfilm, const sgspm_grid* grids, const double* eps, co
 /* Uniform applied field per film (3*nfilm doubles); clears any per-cell h_e. */
 int sgspm_set_applied_field(sgspm_t h, const double* he);
 
+/* Damping alpha per film (nfilm doubles, finite, >= 0), e.g. between a recorded forward and the
+ * next; the kernels read it at run time, so captured steps pick it up.  ERR_ARG otherwise. */
+int sgspm_set_alpha(sgspm_t h, const double* alpha);
+
 /* Copy a field in (SGSPM_M, SGSPM_HE).  ptr: host or device, layout as above, dtype F32/F64. */
 int sgspm_set_field(sgspm_t h, int which, const void* ptr, int dtype);
 

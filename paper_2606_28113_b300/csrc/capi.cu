@@ -1587,6 +1587,16 @@ int sgspm_set_applied_field(sgspm_t ctx, const double* he) {
     return SGSPM_OK;
 }
 
+int sgspm_set_alpha(sgspm_t ctx, const double* alpha) {
+    if (!ctx || !alpha) return ctx ? fail(ctx, SGSPM_ERR_ARG, "alpha is NULL") : SGSPM_ERR_ARG;
+    for (int f = 0; f < ctx->nfilm; ++f)
+        if (!(std::isfinite(alpha[f]) && alpha[f] >= 0)) return fail(ctx, SGSPM_ERR_ARG, "alpha must be finite and >= 0");
+    for (int f = 0; f < ctx->nfilm; ++f) ctx->films[f].alpha = alpha[f];
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
+    return SGSPM_OK;
+}
+
 int sgspm_set_field(sgspm_t ctx, int which, const void* ptr, int dtype) {
     if (!ctx) return SGSPM_ERR_ARG;
     if (!ptr) return fail(ctx, SGSPM_ERR_ARG, "ptr is NULL");

@@ -48,6 +48,7 @@ def lib():
     L.sgspm_create.argtypes = [ctypes.POINTER(Grid), d, d, d, d, dp, i, vp, ctypes.POINTER(vp)]
     L.sgspm_create_batch.argtypes = [i, ctypes.POINTER(Grid), dp, dp, dp, dp, dp, i, vp, ctypes.POINTER(vp)]
     L.sgspm_set_applied_field.argtypes = [vp, dp]
+    L.sgspm_set_alpha.argtypes = [vp, dp]
     L.sgspm_set_field.argtypes = [vp, i, vp, i]
     L.sgspm_get_field.argtypes = [vp, i, vp, i]
     L.sgspm_step.argtypes = [vp, ll]
@@ -70,7 +71,7 @@ def lib():
     L.sgspm_energy_noalloc.restype = ctypes.c_int
     L.sgspm_noalloc_last_error.argtypes = []
     L.sgspm_noalloc_last_error.restype = ctypes.c_char_p
-    for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_field",
+    for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_alpha", "sgspm_set_field",
                  "sgspm_get_field", "sgspm_step", "sgspm_energy", "sgspm_set_forcing", "sgspm_set_time",
                  "sgspm_get_time", "sgspm_sync", "sgspm_destroy", "sgspm_launches_per_step", "sgspm_version",
                  "sgspm_profile_step"):
@@ -186,6 +187,14 @@ class Handle:
         he = np.ascontiguousarray(np.asarray(he, dtype=np.float64).reshape(-1))
         self._check(lib().sgspm_set_applied_field(self.h, _dptr(he)))
 
+    def set_alpha(self, alpha):
+        """Damping alpha per film (a scalar sets every film)."""
+        a = np.broadcast_to(np.asarray(alpha, dtype=np.float64).reshape(-1), (len(self.films),))
+        a = np.ascontiguousarray(a)
+        self._check(lib().sgspm_set_alpha(self.h, _dptr(a)))
+        for f, v in zip(self.films, a):
+            f["alpha"] = float(v)
+
     def set_field(self, which, x):
         p, code, keep = _buffer(x)
         self._check(lib().sgspm_set_field(self.h, which, p, code))
@@ -269,6 +278,49 @@ class Handle:
         if n < 0:
             self._check(n)
         return [(kind[i], ms[i]) for i in range(n)]
+
+
+def _trajectory_function():
+    import torch
+
+    class Trajectory(torch.autograd.Function):
+        """m(T) after `steps` SGSPM steps from m0, differentiable in the per-cell applied field and
+        alpha: forward = sgspm_record (checkpoints every K steps), backward = sgspm_grad."""
+
+        @staticmethod
+        def forward(ctx, he, alpha, handle, m0, steps, K):
+            handle.set_alpha(alpha.detach().double().cpu().numpy())
+            handle.set_m(m0)
+            handle.set_he(he.detach().contiguous())
+            handle.record(steps, K)
+            mT = torch.empty(3 * handle.total_cells, dtype=he.dtype, device=he.device)
+            handle.get_m(mT)
+            ctx.handle = handle
+            ctx.alpha_meta = (alpha.shape, alpha.dtype, alpha.device)
+            return mT
+
+        @staticmethod
+        def backward(ctx, g_mT):
+            g_he = torch.empty_like(g_mT)
+            _, g_alpha = ctx.handle.grad(g_mT.contiguous(), g_he)
+            shape, dtype, device = ctx.alpha_meta
+            g_a = torch.as_tensor(g_alpha, dtype=dtype, device=device).reshape(shape)
+            return g_he, g_a, None, None, None, None
+
+    return Trajectory
+
+
+_Trajectory = None
+
+
+def trajectory(handle, m0, he, alpha, steps, K=50):
+    """Differentiable m(T) (flat field layout, dtype and device of `he`) of `handle` from m0 under
+    the per-cell applied field `he` (torch tensor, 3 x cells) and damping `alpha` (torch tensor: a
+    scalar, or one per film).  Gradients flow to `he` and `alpha` through the hand-written adjoint."""
+    global _Trajectory
+    if _Trajectory is None:
+        _Trajectory = _trajectory_function()
+    return _Trajectory.apply(he, alpha, handle, m0, int(steps), int(K))
 
 
 def energy_noalloc(n, h, eps, Q, u, he, m, hs, out, stream=None):

@@ -103,3 +103,26 @@ def test_film128x128x4_against_central_differences(steps, check_alpha):
         assert abs(dv - fd_v) <= tol * abs(fd_v)
         if check_alpha:
             assert abs(a - fd_a) <= tol * abs(fd_a)
+
+
+def test_autograd_function_matches_torch_reference():
+    """sgspm.trajectory (torch.autograd.Function over record/grad) against autograd through the
+    plain torch FP64 step: loss, dL/dh_e per cell and dL/dalpha."""
+    n, h = (16, 16, 2), (1 / 16,) * 3
+    kw = dict(eps=0.016, Q=6.2e-4, dt=0.01)
+    m0 = inputs.random_unit(6, n)
+    he0 = 0.02 * np.random.default_rng(7).normal(size=(3, n[2], n[1], n[0]))
+    steps, K = 10, 4
+    model = torch_step.TorchSGSPM(n, h, **kw)
+    L_ref, g_ref, a_ref = torch_step.reference_gradients(model, m0, he0, 0.01, steps, REG)
+    H = sgspm.film(n, h, alpha=0.03, fp64=True, **kw)   # alpha is set by the Function's input
+    he = torch.tensor(he0.reshape(-1), dtype=torch.float64, device="cuda", requires_grad=True)
+    alpha = torch.tensor(0.01, dtype=torch.float64, requires_grad=True)
+    mT = sgspm.trajectory(H, m0, he, alpha, steps, K).reshape(3, n[2], n[1], n[0])
+    L = torch.mean((mT[0] - 1.0) ** 2) + REG * torch.sum(he * he)
+    L.backward()
+    H.close()
+    assert abs(L.item() - L_ref) <= 1e-12
+    g = he.grad.cpu().numpy().reshape(3, n[2], n[1], n[0])
+    assert np.abs(g - g_ref).max() <= 1e-10 * np.abs(g_ref).max()
+    assert abs(alpha.grad.item() - a_ref) <= 1e-10 * abs(a_ref)
