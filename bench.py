@@ -199,13 +199,14 @@ def run_ensemble(sgspm, torch, stream, steps, warmup=3):
             "launches_per_step": lps, "launch_shares": {str(k): v / tot for k, v in sorted(prof.items())}}
 
 
-def run_strip(sgspm, torch, stream, steps):
+def run_strip(sgspm, torch, stream, steps, tf32x3=True):
     """The 512x64x4 strip with a Neel wall (h = 0.1, Q = 0.1, h_e = 0.005 along +x, alpha = 1e-2,
-    dt = 0.005), FP32 form: cell-steps/s and the wall's displacement (zero of <m_x>(x), cells)."""
+    dt = 0.005), TF32X3 form (else FP32): cell-steps/s and the wall's displacement (zero of
+    <m_x>(x), cells)."""
     w = dict(inputs.WORKLOADS["strip512x64x4_wall"], alpha=1e-2)
     m0 = inputs.initial_state(w)
     H = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
-                   stream=stream.cuda_stream)
+                   stream=stream.cuda_stream, tf32x3=tf32x3)
     H.set_m(m0)
     H.step(3)
     H.sync()
@@ -224,7 +225,8 @@ def run_strip(sgspm, torch, stream, steps):
     x1 = wall(H.split(H.get_m())[0])
     H.close()
     ncell = int(np.prod(w["n"]))
-    return {"workload": "strip512x64x4_wall (Neel wall, alpha 1e-2)", "cells": ncell, "dtype": "f32",
+    return {"workload": "strip512x64x4_wall (Neel wall, alpha 1e-2)", "cells": ncell,
+            "form": "tf32x3 (z DCTs on tcgen05)" if tf32x3 else "fp32", "dtype": "f32",
             "value": ncell * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
             "wall_displacement_cells": x1 - wall(m0), "after_steps": steps + 3,
             "l2": "not flushed (working set in L2)"}
@@ -244,7 +246,7 @@ def run_gpu(args):
     m0 = inputs.initial_state(dict(w, seed=w["seed"] + rank))
     stream = torch.cuda.current_stream()
     H = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
-                   stream=stream.cuda_stream)
+                   stream=stream.cuda_stream, tf32x3=(args.form == "tf32x3"))
     m0_t = torch.from_numpy(m0.astype(np.float32).reshape(-1)).cuda()
     H.set_m(m0_t)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -313,9 +315,20 @@ def run_gpu(args):
                     stream=stream.cuda_stream)
     Hb = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=True,
                     stream=stream.cuda_stream)
+    Hc = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
+                    stream=stream.cuda_stream, tf32x3=True)
     Ha.set_m(m0)
     Hb.set_m(m0)
+    Hc.set_m(m0)
     Ha.step(nacc)
+    evc = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    Hc.step(2)
+    Hc.sync()
+    evc[0].record(stream)
+    Hc.step(nacc - 2)
+    evc[1].record(stream)
+    Hc.sync()
+    tc_ms = evc[0].elapsed_time(evc[1]) / (nacc - 2)
     ev64 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     Hb.step(2)
     Hb.sync()
@@ -324,10 +337,15 @@ def run_gpu(args):
     ev64[1].record(stream)
     Hb.sync()
     fp64_ms = ev64[0].elapsed_time(ev64[1]) / (nacc - 2)
-    ma, mb = Ha.get_m(), Hb.get_m()
-    Ea, Eb = Ha.energy()[0], Hb.energy()[0]
+    ma, mb, mc = Ha.get_m(), Hb.get_m(), Hc.get_m()
+    Ea, Eb, Ec = Ha.energy()[0], Hb.energy()[0], Hc.energy()[0]
     Ha.close()
     Hb.close()
+    Hc.close()
+    tc_form = {"ms_per_step": tc_ms, "value": ncell / (tc_ms / 1e3), "unit": UNIT,
+               "accuracy_vs_fp64_form": {"steps": nacc, "max_abs_dm": float(np.abs(mc - mb).max()),
+                                         "rel_energy_err": float(abs(Ec[4] - Eb[4]) / abs(Eb[4]))},
+               "note": "not L2-flushed; z DCTs as 3xTF32 GEMMs on tcgen05"}
     max_dm = float(np.abs(ma - mb).max())
     rel_e = float(abs(Ea[4] - Eb[4]) / abs(Eb[4]))
 
@@ -347,11 +365,15 @@ def run_gpu(args):
     launches = args.steps * H.launches_per_step()
     H.close()
     ens = run_ensemble(sgspm, torch, stream, args.ensemble_steps) if args.ensemble_steps > 0 else None
-    strip = run_strip(sgspm, torch, stream, args.strip_steps) if args.strip_steps > 0 else None
+    strip = None
+    if args.strip_steps > 0:
+        strip = run_strip(sgspm, torch, stream, args.strip_steps, tf32x3=True)
+        strip["fp32_form"] = run_strip(sgspm, torch, stream, args.strip_steps, tf32x3=False)
 
     if rank == 0:
         cpu, _ = cpu_baseline(w, m0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else (None, None)
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        metric = METRIC if args.form == "fp32" else METRIC.replace("FP32 form", "TF32X3 form")
+        line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": list(w["n"]), "h": w["h"][0], "eps": w["eps"], "Q": w["Q"],
@@ -361,6 +383,7 @@ def run_gpu(args):
                 "step_algorithmic_hbm_frac": step_frac,
                 "fp64_form": {"ms_per_step": fp64_ms, "value": ncell / (fp64_ms / 1e3), "unit": UNIT},
                 "speedup_vs_fp64_form": (fp64_ms / (step_ms / args.steps)),
+                "tf32x3_form": tc_form,
                 "accuracy_vs_fp64_form": {"steps": nacc, "max_abs_dm": max_dm, "rel_energy_err": rel_e},
                 "launch_shares": {str(k): v / total for k, v in sorted(share.items())},
                 "cpu_baseline": cpu,
@@ -382,6 +405,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--form", default="fp32", choices=["fp32", "tf32x3"],
+                    help="form of the timed film: FP32 (default) or TF32X3 (z DCTs on the tensor cores)")
     ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps for cpu_baseline (0: skip)")
     ap.add_argument("--strip-steps", type=int, default=400,
                     help="timed steps of the 512x64x4 Neel-wall strip, reported beside the line (0: skip)")

@@ -70,7 +70,10 @@ enum {
     SGSPM_GSPM = 1 << 1,          /* one-sided GSPM of Sec. 3.1 instead of SGSPM (Sec. 3.2)   */
     SGSPM_NO_STRAY = 1 << 2,      /* h_s = 0                                                 */
     SGSPM_FROZEN_STRAY = 1 << 3,  /* h_s(m^n) for Step 1 and h_s(m**) for Step 2             */
-    SGSPM_NO_GRAPH = 1 << 4       /* launch kernels directly instead of a captured CUDA graph */
+    SGSPM_NO_GRAPH = 1 << 4,      /* launch kernels directly instead of a captured CUDA graph */
+    SGSPM_TF32X3 = 1 << 5         /* FP32 form: short-axis (z) DCTs as 3xTF32 GEMMs on the tensor
+                                     cores (films with nx in {128, 256, 512}, 2 <= nz <= 8; other
+                                     films keep the FP32 path).  Ignored with SGSPM_FP64.  */
 };
 
 /* field selectors */

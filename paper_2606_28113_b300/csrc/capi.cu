@@ -49,6 +49,7 @@ struct sgspm_ctx {
     int flags = 0;
     bool fp64 = false;
     bool stray = true;
+    bool tf32x3 = false;               // TF32X3 form: tensor-core z transforms (FP32 form only)
     cudaStream_t stream = nullptr;     // caller's stream
     cudaStream_t cap = nullptr;        // private capture stream
     std::vector<Film> films;
@@ -222,11 +223,23 @@ static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, 
 
 static int pow2_key(int n, int lo, int hi) { return (n >= lo && n <= hi && (n & (n - 1)) == 0) ? n : 0; }
 
+// size classes whose slab pass runs the tensor-core z transforms in the TF32X3 form
+static bool ztc_class(bool tf32x3, int key) { return tf32x3 && (key == 128 || key == 256 || key == 512); }
+
 template <typename T>
-static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray) {
+static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray,
+                      bool tf32x3) {
     if constexpr (sizeof(T) == 8) {   // the FP64 form uses the runtime-length kernel only
         launch_pdl(xz_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg, stray);
         return;
+    } else {
+        if (ztc_class(tf32x3, key)) {
+            switch (key) {
+                case 128: launch_pdl(xz_kernel<T, 128, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+                case 256: launch_pdl(xz_kernel<T, 256, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+                default: launch_pdl(xz_kernel<T, 512, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+            }
+        }
     }
     switch (key) {
 #define SGSPM_XZ(K) case K: launch_pdl(xz_kernel<T, K>, nb, kThreads, smem, st, d, w, pg, stray); break;
@@ -236,8 +249,18 @@ static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T
     }
 }
 template <typename T>
-static cudaError_t attr_xz(int key, size_t smem) {
-    if constexpr (sizeof(T) == 8) return cudaFuncSetAttribute(xz_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t attr_xz(int key, size_t smem, bool tf32x3) {
+    if constexpr (sizeof(T) == 8) {
+        return cudaFuncSetAttribute(xz_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    } else {
+        if (ztc_class(tf32x3, key)) {
+            switch (key) {
+                case 128: return cudaFuncSetAttribute(xz_kernel<T, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                case 256: return cudaFuncSetAttribute(xz_kernel<T, 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                default: return cudaFuncSetAttribute(xz_kernel<T, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            }
+        }
+    }
     switch (key) {
 #define SGSPM_XZ(K) case K: return cudaFuncSetAttribute(xz_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
@@ -301,7 +324,7 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
     Dev<T> d = dev_view<T>(ctx);
     switch (L.kind) {
         case 0:
-            for (const auto& c : ctx->xz_cls) launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0);
+            for (const auto& c : ctx->xz_cls) launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3);
             break;
         case 1:
             for (const auto& c : ctx->yh_cls) launch_yh<T>(c.key, c.n, c.smem, st, d, c.work, L.y);
@@ -1084,7 +1107,8 @@ static int setup_t(sgspm_ctx* ctx) {
     size_t sx = 0, sy = 0;
     int maxPy = 1, maxny = 1;
     for (const Film& F : ctx->films) {
-        XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray);
+        const int key = sizeof(T) == 8 ? 0 : pow2_key(F.nx, 8, 512);
+        XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray, ztc_class(ctx->tf32x3, key));
         size_t b = xz_smem_bytes<T>(L);
         if (b > sx) sx = b;
         if (F.Py > maxPy) maxPy = F.Py;
@@ -1126,7 +1150,7 @@ static int setup_t(sgspm_ctx* ctx) {
             for (int y = 0; y < F.ny; ++y) wx[kx].push_back(make_int4(f, y, 0, 0));
             for (int kz = 0; kz < F.nz; ++kz)
                 for (int x0 = 0; x0 < F.nx; x0 += ctx->tx_h) wy[ky].push_back(make_int4(f, kz, x0, std::min(ctx->tx_h, F.nx - x0)));
-            XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray);
+            XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray, ztc_class(ctx->tf32x3, kx));
             sxk[kx] = std::max(sxk[kx], xz_smem_bytes<T>(L));
             syk[ky] = std::max(syk[ky], (size_t)2 * F.ny * V + (size_t)2 * ((ctx->tx_h + 1) / 2) * F.ny * V +
                                             (size_t)ctx->tx_h * (F.ny + 8) * sizeof(T));
@@ -1137,7 +1161,7 @@ static int setup_t(sgspm_ctx* ctx) {
         for (auto& kv : wx) {
             sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), sxk[kv.first]};
             if ((rc = up4(&c.work, kv.second))) return rc;
-            CK(attr_xz<T>(c.key, c.smem));
+            CK(attr_xz<T>(c.key, c.smem, ctx->tf32x3));
             ctx->xz_cls.push_back(c);
         }
         for (auto& kv : wy) {
@@ -1270,6 +1294,7 @@ static int check_status(sgspm_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
     if (st & 1) return fail(ctx, SGSPM_ERR_NONFINITE, "non-finite value or zero vector before projection");
     if (st & 2) return fail(ctx, SGSPM_ERR_NONFINITE, "set_field: zero-length or non-finite magnetisation vector");
+    if (st & 4) return fail(ctx, SGSPM_ERR_TIMEOUT, "a tensor-core transform of the slab pass did not complete in time");
     return SGSPM_OK;
 }
 
@@ -1512,6 +1537,7 @@ int sgspm_create_batch(int nfilm, const sgspm_grid* grids, const double* eps, co
     ctx->flags = flags;
     ctx->fp64 = (flags & SGSPM_FP64) != 0;
     ctx->stray = !(flags & SGSPM_NO_STRAY);
+    ctx->tf32x3 = (flags & SGSPM_TF32X3) && !ctx->fp64;
     ctx->stream = (cudaStream_t)cuda_stream;
     for (int f = 0; f < nfilm; ++f) {
         const sgspm_grid& g = grids[f];

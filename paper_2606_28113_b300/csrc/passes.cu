@@ -61,7 +61,8 @@ __device__ long long g_phase_clk[64];
 // XZ slab pass
 // ------------------------------------------------------------------------------------------
 // NX: compile-time x length of the films this launch covers (0: any length, runtime transforms)
-template <typename T, int NX>
+// ZTC: TF32X3 form (FP32 only): the z transforms of films with tc_zdct_ok run on the tensor cores
+template <typename T, int NX, bool ZTC = false>
 __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     const Film F = d.films[wi.x];
     const int y = wi.y;
     const int nx = F.nx, ny = F.ny, nz = F.nz, Px = F.Px, Pz = F.Pz, Kx = F.Kx;
-    const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0);
+    const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0, ZTC);
     __shared__ Plan pdx, pdz, ppx, ppz;
     if (threadIdx.x == 0) {
         // pre-staged plan copies (their twiddle offsets refer to the shared layout below)
@@ -100,6 +101,20 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     if (Lo.dt)
         for (int i = threadIdx.x; i < 2 * nz * nz; i += blockDim.x) sdt[i] = d.dtab[F.gdtab_z + i];
     __syncthreads();
+    // TF32X3 form: B operands (forward hi, lo; inverse hi, lo) after the DCT tables, tensor memory
+    const bool tcz = ZTC && tc_zdct_ok(nx, nz);
+    unsigned char* tcb =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sdt + Lo.dt) + 15) & ~(uintptr_t)15);
+    __shared__ uint64_t tc_bar;
+    __shared__ uint32_t tc_slot;
+    TcState tcs{};
+    if constexpr (ZTC) {
+        if (tcz) {
+            tc_write_b(sdt, nz, tcb, tcb + kTcBBytes);
+            tc_write_b(sdt + nz * nz, nz, tcb + 2 * kTcBBytes, tcb + 3 * kTcBBytes);
+        }
+        tc_setup(tcs, &tc_slot, &tc_bar, tc_tmem_cols(NX));
+    }
     pdl_wait();   // everything above reads constant data; fields of the previous pass from here on
     const int S = Lo.slab;
     const int KC = Lo.kc;
@@ -253,7 +268,15 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         PHASE_MARK(4);
         dct2_lines<T, NX>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
         PHASE_MARK(5);
-        if (zreg) {
+        bool zdone = false;
+        if constexpr (ZTC) {
+            if (tcz) {
+                tc_zdct(h, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb, tcb + kTcBBytes, tcs, d.status);
+                zdone = true;
+            }
+        }
+        if (zdone) {
+        } else if (zreg) {
             for (int x = threadIdx.x; x < nx; x += blockDim.x) {
                 T v[kZReg];
 #pragma unroll
@@ -292,7 +315,16 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             s[idx] = in[cell_of(z, x)];
         }
         __syncthreads();
-        if (zreg) {
+        bool zdone = false;
+        if constexpr (ZTC) {
+            if (tcz) {
+                tc_zdct(s, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb + 2 * kTcBBytes, tcb + 3 * kTcBBytes, tcs,
+                        d.status);
+                zdone = true;
+            }
+        }
+        if (zdone) {
+        } else if (zreg) {
             for (int x = threadIdx.x; x < nx; x += blockDim.x) {
                 T v[kZReg];
 #pragma unroll
@@ -525,6 +557,11 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         }
     }
     PHASE_MARK(13);
+    if constexpr (ZTC) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        tc_teardown(tcs, tc_tmem_cols(NX));
+    }
 }
 
 // ------------------------------------------------------------------------------------------

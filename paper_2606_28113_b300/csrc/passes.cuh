@@ -8,6 +8,7 @@
 #pragma once
 #include "common.cuh"
 #include "fft.cuh"
+#include "tc_dct.cuh"
 
 namespace sgspm {
 
@@ -19,6 +20,7 @@ struct XZLayout {
     int kc;    // kx chunk of the z transforms
     int zw;    // complex elements of each of the two z-work buffers
     int slab;  // real elements of each of the three slabs
+    int tc;    // bytes of the tensor-core B operands (TF32X3 form), 16-byte aligned, else 0
 };
 
 // Thin films (nz <= kZReg) transform along z in registers, one thread per column: dense
@@ -27,7 +29,8 @@ constexpr int kZReg = 8;
 
 __host__ __device__ inline bool z_in_registers(int nz) { return nz <= kZReg; }
 
-__host__ __device__ inline XZLayout xz_layout(int nx, int nz, int Px, int Pz, int Kx, bool stray) {
+// ztc: the TF32X3 form's tensor-core z transforms (operand A reuses the two x-work buffers)
+__host__ __device__ inline XZLayout xz_layout(int nx, int nz, int Px, int Pz, int Kx, bool stray, bool ztc = false) {
     XZLayout L;
     const bool zreg = z_in_registers(nz);
     int a = ((nz + 1) / 2) * nx;
@@ -40,12 +43,17 @@ __host__ __device__ inline XZLayout xz_layout(int nx, int nz, int Px, int Pz, in
     L.slab = nx * nz;
     L.tw = 2 * nx + 2 * nz + (stray ? Px + Pz : 0);
     L.dt = zreg ? ((2 * nz * nz + 1) / 2) * 2 : 0;   // even count keeps the complex buffers aligned
+    L.tc = 0;
+    if (ztc && tc_zdct_ok(nx, nz)) {
+        if (L.xw < 4 * nx) L.xw = 4 * nx;   // 2 (hi, lo) x nx/128 tiles of 4 KiB in xw0..xw1
+        L.tc = 4 * kTcBBytes + 16;          // forward and inverse tables, hi and lo, + alignment
+    }
     return L;
 }
 
 template <typename T>
 __host__ __device__ inline size_t xz_smem_bytes(const XZLayout& L) {
-    return (size_t)(L.tw + 2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)(3 * L.slab + L.dt) * sizeof(T);
+    return (size_t)(L.tw + 2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)(3 * L.slab + L.dt) * sizeof(T) + (size_t)L.tc;
 }
 
 // Copy the twiddle tables of `pl` (W_P, and the DCT quarter-wave table when `dct`) from the

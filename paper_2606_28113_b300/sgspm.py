@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libsgspm.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, GSPM, NO_STRAY, FROZEN_STRAY, NO_GRAPH = 1, 2, 4, 8, 16
+FP64, GSPM, NO_STRAY, FROZEN_STRAY, NO_GRAPH, TF32X3 = 1, 2, 4, 8, 16, 32
 M, HE, HS = 0, 1, 2
 F32, F64 = 0, 1
 FORCE_NONE, FORCE_MMS_1D, FORCE_MMS_3D = 0, 1, 3
@@ -101,8 +101,10 @@ def _buffer(x):
     return ctypes.c_void_p(a.ctypes.data), (F64 if a.dtype == np.float64 else F32), a
 
 
-def _flags(fp64, scheme, stray, refresh, graph):
+def _flags(fp64, scheme, stray, refresh, graph, tf32x3=False):
     f = 0
+    if tf32x3:
+        f |= TF32X3
     if fp64:
         f |= FP64
     if scheme == "gspm":
@@ -135,7 +137,8 @@ def _stream(stream):
 class Handle:
     """A handle of one film or of a batch of films (sgspm_create / sgspm_create_batch)."""
 
-    def __init__(self, films, fp64=False, scheme="sgspm", stray=True, refresh="R1", graph=True, stream=None):
+    def __init__(self, films, fp64=False, scheme="sgspm", stray=True, refresh="R1", graph=True, stream=None,
+                 tf32x3=False):
         L = lib()
         self.films = [dict(f) for f in films]
         nf = len(self.films)
@@ -144,7 +147,7 @@ class Handle:
         self._eps, self._Q, self._alpha, self._dt = arr("eps"), arr("Q"), arr("alpha"), arr("dt")
         self._u = np.ascontiguousarray([f.get("u", (1.0, 0.0, 0.0)) for f in self.films], dtype=np.float64).reshape(-1)
         self.fp64 = fp64
-        self.flags = _flags(fp64, scheme, stray, refresh, graph)
+        self.flags = _flags(fp64, scheme, stray, refresh, graph, tf32x3)
         h = ctypes.c_void_p()
         rc = L.sgspm_create_batch(nf, grids, _dptr(self._eps), _dptr(self._Q), _dptr(self._alpha), _dptr(self._dt),
                                   _dptr(self._u), self.flags, _stream(stream), ctypes.byref(h))
