@@ -10,11 +10,10 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["capi.cu"]   # includes passes.cu and newell.cu (one translation unit)
+SOURCES = ["capi.cu"]   # includes passes.cu, newell.cu, noalloc.cu, adjoint.cu (one translation unit)
 LIB = os.path.join(HERE, "libsgspm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--use_fast_math=false",
-         "-Xptxas", "-v"] if False else ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]   # --ptxas adds -Xptxas -v
 
 
 def nvcc():
