@@ -111,6 +111,23 @@ int sgspm_create_batch(int nfilm, const sgspm_grid* grids, const double* eps, co
 /* Uniform applied field per film (3*nfilm doubles); clears any per-cell h_e. */
 int sgspm_set_applied_field(sgspm_t h, const double* he);
 
+/*
+ * Batch packing of the slab pass (no counterpart in the paper: a launch-shape choice).  Films are
+ * grouped in size classes by nx; a class of small slabs (FP32 form, nx <= 128 or not a power of
+ * two, not TF32X3) may run several consecutive y rows of a film per CTA.
+ * sgspm_xz_classes: number of classes (>= 0); with keys/rows non-NULL (cap entries) writes each
+ *   class's key (nx, or 0 for the runtime-length kernel) and its current rows per CTA.
+ * sgspm_set_packing: rows per CTA (1..8), one entry per class; ERR_UNSUPPORTED for > 1 on a
+ *   class that runs one row per CTA.  Results do not depend on the packing (bitwise).
+ * sgspm_autotune: times `steps` steps for rows 1, 2, 4, 8 of every packable class and keeps the
+ *   fastest; m and the step count are restored afterwards (it allocates a copy of m while it
+ *   runs).  Needs m set (ERR_STATE).  Writes the chosen rows to rows_out (cap entries) when
+ *   non-NULL and returns the number of classes.
+ */
+int sgspm_xz_classes(sgspm_t h, int* keys, int* rows, int cap);
+int sgspm_set_packing(sgspm_t h, const int* rows, int n);
+int sgspm_autotune(sgspm_t h, int steps, int* rows_out, int cap);
+
 /* Damping alpha per film (nfilm doubles, finite, >= 0), e.g. between a recorded forward and the
  * next; the kernels read it at run time, so captured steps pick it up.  ERR_ARG otherwise. */
 int sgspm_set_alpha(sgspm_t h, const double* alpha);

@@ -93,6 +93,7 @@ struct sgspm_ctx {
         int4* work;
         int n;
         size_t smem;
+        int rows = 1;                  // slab pass: y rows per CTA (batch packing)
     };
     std::vector<KClass> xz_cls, yh_cls, yw_cls;
     int4* d_work_xz = nullptr;
@@ -226,13 +227,27 @@ static int pow2_key(int n, int lo, int hi) { return (n >= lo && n <= hi && (n & 
 // size classes whose slab pass runs the tensor-core z transforms in the TF32X3 form
 static bool ztc_class(bool tf32x3, int key) { return tf32x3 && (key == 128 || key == 256 || key == 512); }
 
+constexpr int kMaxRowsPerCTA = 8;   // slab pass packing: y rows of one film per CTA
+
+// size classes whose slab pass may pack several y rows per CTA (FP32 form; small slabs)
+static bool packable_class(bool fp64, bool tf32x3, int key) {
+    return !fp64 && !ztc_class(tf32x3, key) && (key == 0 || key == 8 || key == 16 || key == 32 || key == 64 || key == 128);
+}
+
 template <typename T>
 static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray,
-                      bool tf32x3) {
+                      bool tf32x3, int rows) {
     if constexpr (sizeof(T) == 8) {   // the FP64 form uses the runtime-length kernel only
         launch_pdl(xz_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg, stray);
         return;
     } else {
+        if (rows > 1) {
+            switch (key) {
+                case 64: launch_pdl(xz_kernel<T, 64, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+                case 128: launch_pdl(xz_kernel<T, 128, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+                default: launch_pdl(xz_kernel<T, 0, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+            }
+        }
         if (ztc_class(tf32x3, key)) {
             switch (key) {
                 case 128: launch_pdl(xz_kernel<T, 128, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
@@ -253,6 +268,22 @@ static cudaError_t attr_xz(int key, size_t smem, bool tf32x3) {
     if constexpr (sizeof(T) == 8) {
         return cudaFuncSetAttribute(xz_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     } else {
+        if (packable_class(false, tf32x3, key)) {
+            cudaError_t e;
+            if (key == 64) {
+                e = cudaFuncSetAttribute(xz_kernel<T, 64, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            } else if (key == 128) {
+                e = cudaFuncSetAttribute(xz_kernel<T, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            } else {
+                // shared by several classes (runtime x length): allow the device's opt-in maximum
+                int dev = 0, mx = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+                e = cudaFuncSetAttribute(xz_kernel<T, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max(mx, (int)smem));
+            }
+            if (e != cudaSuccess) return e;
+        }
         if (ztc_class(tf32x3, key)) {
             switch (key) {
                 case 128: return cudaFuncSetAttribute(xz_kernel<T, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -324,7 +355,8 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
     Dev<T> d = dev_view<T>(ctx);
     switch (L.kind) {
         case 0:
-            for (const auto& c : ctx->xz_cls) launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3);
+            for (const auto& c : ctx->xz_cls)
+                launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3, c.rows);
             break;
         case 1:
             for (const auto& c : ctx->yh_cls) launch_yh<T>(c.key, c.n, c.smem, st, d, c.work, L.y);
@@ -1658,6 +1690,123 @@ int sgspm_step(sgspm_t ctx, long long n) {
     }
     ctx->steps += n;
     return SGSPM_OK;
+}
+
+// ---- batch packing and its autotuner ----------------------------------------------------------
+static int xz_class_key(const sgspm_ctx* ctx, const Film& F) { return ctx->fp64 ? 0 : pow2_key(F.nx, 8, 512); }
+
+// Rebuild the slab-pass work list of class c with `rows` y rows per CTA.
+static int set_class_rows(sgspm_ctx* ctx, size_t c, int rows) {
+    auto& K = ctx->xz_cls[c];
+    std::vector<int4> w;
+    for (int f = 0; f < ctx->nfilm; ++f) {
+        const Film& F = ctx->films[f];
+        if (xz_class_key(ctx, F) != K.key) continue;
+        for (int y = 0; y < F.ny; y += rows) w.push_back(make_int4(f, y, std::min(rows, F.ny - y), 0));
+    }
+    int4* d = nullptr;
+    CK(cudaMalloc(&d, std::max<size_t>(1, w.size()) * sizeof(int4)));
+    CK(cudaMemcpy(d, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(K.work);
+    K.work = d;
+    K.n = (int)w.size();
+    K.rows = rows;
+    drop_graph(ctx);
+    return SGSPM_OK;
+}
+
+int sgspm_xz_classes(sgspm_t ctx, int* keys, int* rows, int cap) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    const int n = (int)ctx->xz_cls.size();
+    if ((keys || rows) && cap < n) return fail(ctx, SGSPM_ERR_ARG, "cap is below the number of size classes");
+    for (int c = 0; c < n; ++c) {
+        if (keys) keys[c] = ctx->xz_cls[c].key;
+        if (rows) rows[c] = ctx->xz_cls[c].rows;
+    }
+    return n;
+}
+
+int sgspm_set_packing(sgspm_t ctx, const int* rows, int n) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!rows || n != (int)ctx->xz_cls.size()) return fail(ctx, SGSPM_ERR_ARG, "rows must have one entry per size class");
+    for (int c = 0; c < n; ++c) {
+        if (rows[c] < 1 || rows[c] > kMaxRowsPerCTA) return fail(ctx, SGSPM_ERR_ARG, "rows per CTA must be in 1..8");
+        if (rows[c] > 1 && !packable_class(ctx->fp64, ctx->tf32x3, ctx->xz_cls[c].key))
+            return fail(ctx, SGSPM_ERR_UNSUPPORTED, "this size class runs one row per CTA");
+    }
+    for (int c = 0; c < n; ++c)
+        if (rows[c] != ctx->xz_cls[c].rows) {
+            int rc = set_class_rows(ctx, (size_t)c, rows[c]);
+            if (rc) return rc;
+        }
+    return SGSPM_OK;
+}
+
+int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (steps < 1) return fail(ctx, SGSPM_ERR_ARG, "steps must be >= 1");
+    if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
+    const int ncls = (int)ctx->xz_cls.size();
+    if (rows_out && cap < ncls) return fail(ctx, SGSPM_ERR_ARG, "cap is below the number of size classes");
+    // keep the state: m (hi and lo parts) and the step counters; restored at the end
+    const size_t es = ctx->fp64 ? sizeof(double) : sizeof(float);
+    const size_t fb = (size_t)ctx->ncell * es;
+    void* keep = nullptr;
+    CK(cudaMalloc(&keep, 6 * fb + sizeof(long long)));
+    char* kp = (char*)keep;
+    for (int i = 0; i < 3; ++i) {
+        CK(cudaMemcpyAsync(kp + i * fb, ctx->d_field[M1 + i], fb, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (ctx->d_flo[M1 + i]) CK(cudaMemcpyAsync(kp + (3 + i) * fb, ctx->d_flo[M1 + i], fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(kp + 6 * fb, ctx->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, ctx->stream));
+    const long long steps0 = ctx->steps;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = SGSPM_OK;
+    for (int c = 0; c < ncls && !rc; ++c) {
+        if (!packable_class(ctx->fp64, ctx->tf32x3, ctx->xz_cls[c].key)) continue;
+        int maxny = 1;
+        for (const Film& F : ctx->films)
+            if (xz_class_key(ctx, F) == ctx->xz_cls[c].key) maxny = std::max(maxny, F.ny);
+        float best = 1e30f;
+        int best_rows = 1;
+        for (int r = 1; r <= kMaxRowsPerCTA && r <= maxny && !rc; r *= 2) {
+            if ((rc = set_class_rows(ctx, (size_t)c, r))) break;
+            if ((rc = sgspm_step(ctx, 1))) break;   // captures the graph of this packing
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = SGSPM_ERR_CUDA; break; }
+            if ((rc = sgspm_step(ctx, steps))) break;
+            if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = SGSPM_ERR_CUDA;
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_rows = r;
+            }
+        }
+        if (!rc) rc = set_class_rows(ctx, (size_t)c, best_rows);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < 3; ++i) {
+        CK(cudaMemcpyAsync(ctx->d_field[M1 + i], kp + i * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (ctx->d_flo[M1 + i]) CK(cudaMemcpyAsync(ctx->d_flo[M1 + i], kp + (3 + i) * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(ctx->d_step, kp + 6 * fb, sizeof(long long), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->steps = steps0;
+    int rc2 = run_prog(ctx, ctx->fwd_prog, ctx->stream);   // spectra of the restored state
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(keep);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    rc = check_status(ctx);
+    if (rc) return rc;
+    for (int c = 0; rows_out && c < ncls; ++c) rows_out[c] = ctx->xz_cls[c].rows;
+    return ncls;
 }
 
 int sgspm_energy(sgspm_t ctx, double* out) {

@@ -62,7 +62,9 @@ __device__ long long g_phase_clk[64];
 // ------------------------------------------------------------------------------------------
 // NX: compile-time x length of the films this launch covers (0: any length, runtime transforms)
 // ZTC: TF32X3 form (FP32 only): the z transforms of films with tc_zdct_ok run on the tensor cores
-template <typename T, int NX, bool ZTC = false>
+// MULTI: a work item covers rows y0 .. y0 + w - 1 of one film (packing of small slabs); the
+//        single-row kernels keep the loop at one compile-time trip
+template <typename T, int NX, bool ZTC = false, bool MULTI = false>
 __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     pdl_launch_dependents();
     const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
-    const int y = wi.y;
+    const int y0 = wi.y, nrow = MULTI ? (wi.z > 0 ? wi.z : 1) : 1;
     const int nx = F.nx, ny = F.ny, nz = F.nz, Px = F.Px, Pz = F.Pz, Kx = F.Kx;
     const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0, ZTC);
     __shared__ Plan pdx, pdz, ppx, ppz;
@@ -116,447 +118,450 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         tc_setup(tcs, &tc_slot, &tc_bar, tc_tmem_cols(NX));
     }
     pdl_wait();   // everything above reads constant data; fields of the previous pass from here on
-    const int S = Lo.slab;
-    const int KC = Lo.kc;
-    const int npx = (nz + 1) / 2;
-    const int nxz = nx * nz;
-    const long long cbase = F.off_cell;
-    const long long sbase = F.off_spec;
-    auto cell_of = [&](int z, int x) -> long long { return cbase + ((long long)z * ny + y) * nx + x; };
-    PHASE_MARK(0);
-    const bool zreg = z_in_registers(nz);
-    const T* Cz = sdt;                                       // DCT-II  C[k][n]
-    const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
-    const V* twz = stw + ppz.tw;                             // W_Pz^m
+    for (int y = y0; y < y0 + nrow; ++y) {
+        const int S = Lo.slab;
+        const int KC = Lo.kc;
+        const int npx = (nz + 1) / 2;
+        const int nxz = nx * nz;
+        const long long cbase = F.off_cell;
+        const long long sbase = F.off_spec;
+        auto cell_of = [&](int z, int x) -> long long { return cbase + ((long long)z * ny + y) * nx + x; };
+        PHASE_MARK(0);
+        const bool zreg = z_in_registers(nz);
+        const T* Cz = sdt;                                       // DCT-II  C[k][n]
+        const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
+        const V* twz = stw + ppz.tw;                             // W_Pz^m
 
-    // ---- phase R: right-hand sides and forward DCT ---------------------------------------
-    for (int ci = 0; ci < pg.n_rhs; ++ci) {
-        const int a = pg.rhs_comp[ci];
-        T* h = slabs;   // slab 0
-        if (pg.rhs_copy[ci] >= 0) {
-            // the right-hand side is given (adjoint solves): copy it and transform
-            const T* src = d.field[pg.rhs_copy[ci]];
-            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                int z = idx / nx, x = idx - z * nx;
-                h[idx] = src[cell_of(z, x)];
-            }
-            __syncthreads();
-        } else if (pg.rhs_h[ci] >= 0 && stray) {
-            const V* H = d.spec[pg.rhs_h[ci]] + sbase;
-            if (zreg) {
-                // inverse zero-padded DFT along z in registers, one thread per kx column
-                for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
-                    V acc[kZReg];
-#pragma unroll
-                    for (int z = 0; z < kZReg; ++z) acc[z] = cmk<V>(T(0), T(0));
-                    V hz[2 * kZReg];
-#pragma unroll
-                    for (int kz = 0; kz < 2 * kZReg; ++kz)
-                        hz[kz] = kz < Pz ? H[((long long)kz * ny + y) * Kx + kx] : cmk<V>(T(0), T(0));
-                    if (zfft_reg<T, true>(hz, Pz)) {
-#pragma unroll
-                        for (int z = 0; z < kZReg; ++z) acc[z] = hz[z];
-                    } else {
-#pragma unroll
-                        for (int kz = 0; kz < 2 * kZReg; ++kz) {
-                            if (kz >= Pz) break;
-                            const V hv = hz[kz];
-                            int m = 0;
-#pragma unroll
-                            for (int z = 0; z < kZReg; ++z) {
-                                if (z < nz) acc[z] = cadd(acc[z], cmul(hv, cconj(twz[m])));
-                                m += kz;
-                                if (m >= Pz) m -= Pz;
+        // ---- phase R: right-hand sides and forward DCT ---------------------------------------
+        for (int ci = 0; ci < pg.n_rhs; ++ci) {
+            const int a = pg.rhs_comp[ci];
+            T* h = slabs;   // slab 0
+            if (pg.rhs_copy[ci] >= 0) {
+                // the right-hand side is given (adjoint solves): copy it and transform
+                const T* src = d.field[pg.rhs_copy[ci]];
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                    int z = idx / nx, x = idx - z * nx;
+                    h[idx] = src[cell_of(z, x)];
+                }
+                __syncthreads();
+            } else if (pg.rhs_h[ci] >= 0 && stray) {
+                const V* H = d.spec[pg.rhs_h[ci]] + sbase;
+                if (zreg) {
+                    // inverse zero-padded DFT along z in registers, one thread per kx column
+                    for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
+                        V acc[kZReg];
+    #pragma unroll
+                        for (int z = 0; z < kZReg; ++z) acc[z] = cmk<V>(T(0), T(0));
+                        V hz[2 * kZReg];
+    #pragma unroll
+                        for (int kz = 0; kz < 2 * kZReg; ++kz)
+                            hz[kz] = kz < Pz ? H[((long long)kz * ny + y) * Kx + kx] : cmk<V>(T(0), T(0));
+                        if (zfft_reg<T, true>(hz, Pz)) {
+    #pragma unroll
+                            for (int z = 0; z < kZReg; ++z) acc[z] = hz[z];
+                        } else {
+    #pragma unroll
+                            for (int kz = 0; kz < 2 * kZReg; ++kz) {
+                                if (kz >= Pz) break;
+                                const V hv = hz[kz];
+                                int m = 0;
+    #pragma unroll
+                                for (int z = 0; z < kZReg; ++z) {
+                                    if (z < nz) acc[z] = cadd(acc[z], cmul(hv, cconj(twz[m])));
+                                    m += kz;
+                                    if (m >= Pz) m -= Pz;
+                                }
                             }
                         }
+    #pragma unroll
+                        for (int p = 0; p < kZReg / 2; ++p)
+                            if (2 * p < nz) c2r_put<T>(xw0, p, kx, Px, acc[2 * p], (2 * p + 1 < nz) ? acc[2 * p + 1] : cmk<V>(T(0), T(0)));
                     }
-#pragma unroll
-                    for (int p = 0; p < kZReg / 2; ++p)
-                        if (2 * p < nz) c2r_put<T>(xw0, p, kx, Px, acc[2 * p], (2 * p + 1 < nz) ? acc[2 * p + 1] : cmk<V>(T(0), T(0)));
+                    __syncthreads();
                 }
-                __syncthreads();
+                for (int kc0 = 0; !zreg && kc0 < Kx; kc0 += KC) {
+                    const int kcn = min(KC, Kx - kc0);
+                    for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
+                        int kz = idx / kcn, kc = idx - kz * kcn;
+                        zw0[kz * KC + kc] = H[((long long)kz * ny + y) * Kx + kc0 + kc];
+                    }
+                    __syncthreads();
+                    V* r = fft_lines<T, true>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
+                    for (int idx = threadIdx.x; idx < npx * kcn; idx += blockDim.x) {
+                        int p = idx / kcn, kc = idx - p * kcn;
+                        V xa = r[(2 * p) * KC + kc];
+                        V xb = (2 * p + 1 < nz) ? r[(2 * p + 1) * KC + kc] : cmk<V>(T(0), T(0));
+                        c2r_put<T>(xw0, p, kc0 + kc, Px, xa, xb);
+                    }
+                    __syncthreads();
+                }
+                PHASE_MARK(1);
+                V* r = fft_lines_t<T, true, 2 * NX>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
+                PHASE_MARK(2);
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                    int z = idx / nx, x = idx - z * nx;
+                    V v = r[(z >> 1) * Px + x];
+                    h[idx] = (z & 1) ? v.y : v.x;
+                }
+            } else {
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) h[idx] = T(0);
             }
-            for (int kc0 = 0; !zreg && kc0 < Kx; kc0 += KC) {
-                const int kcn = min(KC, Kx - kc0);
-                for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
-                    int kz = idx / kcn, kc = idx - kz * kcn;
-                    zw0[kz * KC + kc] = H[((long long)kz * ny + y) * Kx + kc0 + kc];
+            __syncthreads();
+            if (pg.rhs_hs_store[ci] >= 0) {
+                T* out = d.field[pg.rhs_hs_store[ci]];
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                    int z = idx / nx, x = idx - z * nx;
+                    out[cell_of(z, x)] = h[idx];
                 }
-                __syncthreads();
-                V* r = fft_lines<T, true>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
-                for (int idx = threadIdx.x; idx < npx * kcn; idx += blockDim.x) {
-                    int p = idx / kcn, kc = idx - p * kcn;
-                    V xa = r[(2 * p) * KC + kc];
-                    V xb = (2 * p + 1 < nz) ? r[(2 * p + 1) * KC + kc] : cmk<V>(T(0), T(0));
-                    c2r_put<T>(xw0, p, kc0 + kc, Px, xa, xb);
-                }
-                __syncthreads();
             }
-            PHASE_MARK(1);
-            V* r = fft_lines_t<T, true, 2 * NX>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
-            PHASE_MARK(2);
+            PHASE_MARK(3);
+            if (!pg.rhs_dct) { __syncthreads(); continue; }
+            // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
+            if (pg.rhs_copy[ci] < 0) {
+                const T* __restrict__ m1 = d.field[pg.state[0]];
+                const T* __restrict__ m2 = d.field[pg.state[1]];
+                const T* __restrict__ m3 = d.field[pg.state[2]];
+                const T* __restrict__ ma = d.field[pg.state[a]];
+                const T scale = T(pg.damp ? F.alpha * F.dt : F.dt);
+                const T eps = T(F.eps), Q = T(F.Q);
+                const T ux = T(F.u[0]), uy = T(F.u[1]), uz = T(F.u[2]);
+                const T ua = T(F.u[a]);
+                const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
+                const T hea = T(F.he[a]);
+                const long long sz = (long long)nx * ny;
+                // batches of kB cells per thread: every load of the batch is issued before any use
+                constexpr int kB = sizeof(T) == 4 ? 4 : 2;
+                for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
+                    // the stencil reads the hi part of a double-float state: its neighbour differences are
+                    // O(h^2 |Delta m|) and the lo parts change them below the FP32 operator rounding
+                    T v1[kB], v2[kB], v3[kB], mc[kB], nb[kB][6];
+    #pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        const int idx = i0 + u * blockDim.x;
+                        if (idx >= nxz) break;
+                        const int z = idx / nx, x = idx - z * nx;
+                        const long long c = cell_of(z, x);
+                        v1[u] = m1[c];
+                        v2[u] = m2[c];
+                        v3[u] = m3[c];
+                        mc[u] = ma[c];
+                        // neighbours with mirror ghosts (a missing neighbour repeats the cell)
+                        const long long o[6] = {x + 1 < nx ? 1 : 0, x > 0 ? -1 : 0, y + 1 < ny ? (long long)nx : 0,
+                                                y > 0 ? -(long long)nx : 0, z + 1 < nz ? sz : 0, z > 0 ? -sz : 0};
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) nb[u][k] = ma[c + o[k]];
+                    }
+    #pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        const int idx = i0 + u * blockDim.x;
+                        if (idx >= nxz) break;
+                        const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
+                        const T mu = v1[u] * ux + v2[u] * uy + v3[u] * uz;
+                        T d6[6];
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) d6[k] = nb[u][k] - mc[u];
+                        const T lap = ihx * (d6[0] + d6[1]) + ihy * (d6[2] + d6[3]) + ihz * (d6[4] + d6[5]);
+                        const T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
+                        const T f = -Q * (mc[u] - mu * ua) + h[idx] + he;
+                        h[idx] = scale * (f + eps * lap);
+                    }
+                }
+            }
+            __syncthreads();
+            PHASE_MARK(4);
+            dct2_lines<T, NX>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
+            PHASE_MARK(5);
+            bool zdone = false;
+            if constexpr (ZTC) {
+                if (tcz) {
+                    tc_zdct(h, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb, tcb + kTcBBytes, tcs, d.status);
+                    zdone = true;
+                }
+            }
+            if (zdone) {
+            } else if (zreg) {
+                for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+                    T v[kZReg];
+    #pragma unroll
+                    for (int z = 0; z < kZReg; ++z) v[z] = z < nz ? h[z * nx + x] : T(0);
+    #pragma unroll
+                    for (int k = 0; k < kZReg; ++k) {
+                        if (k >= nz) break;
+                        T acc = T(0);
+    #pragma unroll
+                        for (int z = 0; z < kZReg; ++z)
+                            if (z < nz) acc += Cz[k * nz + z] * v[z];
+                        h[k * nx + x] = acc;
+                    }
+                }
+                __syncthreads();
+            } else {
+                dct2_lines<T>(h, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
+            }
+            {
+                T* out = d.field[pg.rhs_out[ci]];
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                    int z = idx / nx, x = idx - z * nx;
+                    out[cell_of(z, x)] = h[idx];
+                }
+            }
+            __syncthreads();
+        }
+
+        PHASE_MARK(6);
+        // ---- phase I: inverse DCT of solved spectra -> delta slabs ------------------------------
+        for (int i = 0; i < pg.n_inv; ++i) {
+            T* s = slabs + i * S;
+            const T* in = d.field[pg.inv_in[i]];
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
                 int z = idx / nx, x = idx - z * nx;
-                V v = r[(z >> 1) * Px + x];
-                h[idx] = (z & 1) ? v.y : v.x;
+                s[idx] = in[cell_of(z, x)];
             }
-        } else {
-            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) h[idx] = T(0);
-        }
-        __syncthreads();
-        if (pg.rhs_hs_store[ci] >= 0) {
-            T* out = d.field[pg.rhs_hs_store[ci]];
-            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                int z = idx / nx, x = idx - z * nx;
-                out[cell_of(z, x)] = h[idx];
+            __syncthreads();
+            bool zdone = false;
+            if constexpr (ZTC) {
+                if (tcz) {
+                    tc_zdct(s, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb + 2 * kTcBBytes, tcb + 3 * kTcBBytes, tcs,
+                            d.status);
+                    zdone = true;
+                }
+            }
+            if (zdone) {
+            } else if (zreg) {
+                for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+                    T v[kZReg];
+    #pragma unroll
+                    for (int k = 0; k < kZReg; ++k) v[k] = k < nz ? s[k * nx + x] : T(0);
+    #pragma unroll
+                    for (int z = 0; z < kZReg; ++z) {
+                        if (z >= nz) break;
+                        T acc = T(0);
+    #pragma unroll
+                        for (int k = 0; k < kZReg; ++k)
+                            if (k < nz) acc += Czi[z * nz + k] * v[k];
+                        s[z * nx + x] = acc;
+                    }
+                }
+                __syncthreads();
+            } else {
+                dct3_lines<T>(s, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
+            }
+            PHASE_MARK(7);
+            dct3_lines<T, NX>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
+            PHASE_MARK(8);
+            if (pg.inv_store[i] >= 0) {
+                T* out = d.field[pg.inv_store[i]];
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                    int z = idx / nx, x = idx - z * nx;
+                    out[cell_of(z, x)] = s[idx];
+                }
             }
         }
-        PHASE_MARK(3);
-        if (!pg.rhs_dct) { __syncthreads(); continue; }
-        // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
-        if (pg.rhs_copy[ci] < 0) {
-            const T* __restrict__ m1 = d.field[pg.state[0]];
-            const T* __restrict__ m2 = d.field[pg.state[1]];
-            const T* __restrict__ m3 = d.field[pg.state[2]];
-            const T* __restrict__ ma = d.field[pg.state[a]];
-            const T scale = T(pg.damp ? F.alpha * F.dt : F.dt);
-            const T eps = T(F.eps), Q = T(F.Q);
-            const T ux = T(F.u[0]), uy = T(F.u[1]), uz = T(F.u[2]);
-            const T ua = T(F.u[a]);
-            const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
-            const T hea = T(F.he[a]);
-            const long long sz = (long long)nx * ny;
-            // batches of kB cells per thread: every load of the batch is issued before any use
+
+        PHASE_MARK(9);
+        // ---- phase U: pointwise updates ----------------------------------------------------------
+        if (pg.op == 1) {
+            // Gauss-Seidel cross product: out = base + p*q - r*s  (delta form, see host program)
+            T* out = d.field[pg.gs_out];
+            T* outl = d.flo[pg.gs_out];
+            T* res = slabs + 2 * S;
+            const T* bl_ = pg.gs_base >= 0 ? d.flo[pg.gs_base] : nullptr;
+            const T* ql_ = pg.gs_q >= 0 ? d.flo[pg.gs_q] : nullptr;
+            const T* sl_ = pg.gs_s >= 0 ? d.flo[pg.gs_s] : nullptr;
             constexpr int kB = sizeof(T) == 4 ? 4 : 2;
             for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
-                // the stencil reads the hi part of a double-float state: its neighbour differences are
-                // O(h^2 |Delta m|) and the lo parts change them below the FP32 operator rounding
-                T v1[kB], v2[kB], v3[kB], mc[kB], nb[kB][6];
-#pragma unroll
-                for (int u = 0; u < kB; ++u) {
-                    const int idx = i0 + u * blockDim.x;
-                    if (idx >= nxz) break;
-                    const int z = idx / nx, x = idx - z * nx;
-                    const long long c = cell_of(z, x);
-                    v1[u] = m1[c];
-                    v2[u] = m2[c];
-                    v3[u] = m3[c];
-                    mc[u] = ma[c];
-                    // neighbours with mirror ghosts (a missing neighbour repeats the cell)
-                    const long long o[6] = {x + 1 < nx ? 1 : 0, x > 0 ? -1 : 0, y + 1 < ny ? (long long)nx : 0,
-                                            y > 0 ? -(long long)nx : 0, z + 1 < nz ? sz : 0, z > 0 ? -sz : 0};
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) nb[u][k] = ma[c + o[k]];
-                }
-#pragma unroll
+                T bb[kB], pp[kB], qq[kB], rr[kB], ss[kB], bl[kB], ql[kB], sl[kB];
+    #pragma unroll
                 for (int u = 0; u < kB; ++u) {
                     const int idx = i0 + u * blockDim.x;
                     if (idx >= nxz) break;
                     const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
-                    const T mu = v1[u] * ux + v2[u] * uy + v3[u] * uz;
-                    T d6[6];
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) d6[k] = nb[u][k] - mc[u];
-                    const T lap = ihx * (d6[0] + d6[1]) + ihy * (d6[2] + d6[3]) + ihz * (d6[4] + d6[5]);
-                    const T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
-                    const T f = -Q * (mc[u] - mu * ua) + h[idx] + he;
-                    h[idx] = scale * (f + eps * lap);
+                    bb[u] = load_ref(d, pg.gs_base, c, slabs, S, idx);
+                    pp[u] = load_ref(d, pg.gs_p, c, slabs, S, idx);
+                    qq[u] = load_ref(d, pg.gs_q, c, slabs, S, idx);
+                    rr[u] = load_ref(d, pg.gs_r, c, slabs, S, idx);
+                    ss[u] = load_ref(d, pg.gs_s, c, slabs, S, idx);
+                    bl[u] = bl_ ? bl_[c] : T(0);
+                    ql[u] = ql_ ? ql_[c] : T(0);
+                    sl[u] = sl_ ? sl_[c] : T(0);
                 }
-            }
-        }
-        __syncthreads();
-        PHASE_MARK(4);
-        dct2_lines<T, NX>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
-        PHASE_MARK(5);
-        bool zdone = false;
-        if constexpr (ZTC) {
-            if (tcz) {
-                tc_zdct(h, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb, tcb + kTcBBytes, tcs, d.status);
-                zdone = true;
-            }
-        }
-        if (zdone) {
-        } else if (zreg) {
-            for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-                T v[kZReg];
-#pragma unroll
-                for (int z = 0; z < kZReg; ++z) v[z] = z < nz ? h[z * nx + x] : T(0);
-#pragma unroll
-                for (int k = 0; k < kZReg; ++k) {
-                    if (k >= nz) break;
-                    T acc = T(0);
-#pragma unroll
-                    for (int z = 0; z < kZReg; ++z)
-                        if (z < nz) acc += Cz[k * nz + z] * v[z];
-                    h[k * nx + x] = acc;
+    #pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int idx = i0 + u * blockDim.x;
+                    if (idx >= nxz) break;
+                    const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
+                    if (outl) {
+                        // double-float state: base (hi, lo) + increment p (q_hi + q_lo) - r (s_hi + s_lo)
+                        const T rs = fma(rr[u], sl[u], rr[u] * ss[u]);
+                        const T inc = fma(pp[u], qq[u], fma(pp[u], ql[u], -rs));
+                        T hi, e;
+                        two_sum(bb[u], inc, hi, e);
+                        T h2, l2;
+                        fast_two_sum(hi, e + bl[u], h2, l2);
+                        out[c] = h2;
+                        outl[c] = l2;
+                        res[idx] = h2;
+                    } else {
+                        const T v = bb[u] + (pp[u] * qq[u] - rr[u] * ss[u]);
+                        out[c] = v;
+                        res[idx] = v;
+                    }
                 }
             }
             __syncthreads();
-        } else {
-            dct2_lines<T>(h, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
-        }
-        {
-            T* out = d.field[pg.rhs_out[ci]];
+        } else if (pg.op == 2) {
+            // Step 2 + Step 3: m*** = m** + delta (+ dt f_e), m^{n+1} = m*** / |m***|
+            const double tnow = F.t0 + (double)(*d.step_ctr) * F.dt;
+            const bool dfl = d.flo[pg.fin_out[0]] != nullptr;
             for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
                 int z = idx / nx, x = idx - z * nx;
-                out[cell_of(z, x)] = h[idx];
-            }
-        }
-        __syncthreads();
-    }
-
-    PHASE_MARK(6);
-    // ---- phase I: inverse DCT of solved spectra -> delta slabs ------------------------------
-    for (int i = 0; i < pg.n_inv; ++i) {
-        T* s = slabs + i * S;
-        const T* in = d.field[pg.inv_in[i]];
-        for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-            int z = idx / nx, x = idx - z * nx;
-            s[idx] = in[cell_of(z, x)];
-        }
-        __syncthreads();
-        bool zdone = false;
-        if constexpr (ZTC) {
-            if (tcz) {
-                tc_zdct(s, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb + 2 * kTcBBytes, tcb + 3 * kTcBBytes, tcs,
-                        d.status);
-                zdone = true;
-            }
-        }
-        if (zdone) {
-        } else if (zreg) {
-            for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-                T v[kZReg];
-#pragma unroll
-                for (int k = 0; k < kZReg; ++k) v[k] = k < nz ? s[k * nx + x] : T(0);
-#pragma unroll
-                for (int z = 0; z < kZReg; ++z) {
-                    if (z >= nz) break;
-                    T acc = T(0);
-#pragma unroll
-                    for (int k = 0; k < kZReg; ++k)
-                        if (k < nz) acc += Czi[z * nz + k] * v[k];
-                    s[z * nx + x] = acc;
+                long long c = cell_of(z, x);
+                if (dfl) {
+                    // m*** = m** + delta in double-float, then |m***|^-1 by one double-float Newton step
+                    T h[3], l[3];
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        T s1, e1;
+                        two_sum(d.field[pg.fin_in[i]][c], slabs[i * S + idx], s1, e1);
+                        fast_two_sum(s1, e1 + d.flo[pg.fin_in[i]][c], h[i], l[i]);
+                    }
+                    if (F.forcing) {
+                        double fe[3];
+                        mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
+    #pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            double v = (double)h[i] + (double)l[i] + F.dt * fe[i];
+                            h[i] = (T)v;
+                            l[i] = (T)(v - (double)h[i]);
+                        }
+                    }
+                    T p0, e0, p1, e1, p2, e2;
+                    two_prod(h[0], h[0], p0, e0);
+                    two_prod(h[1], h[1], p1, e1);
+                    two_prod(h[2], h[2], p2, e2);
+                    T s1, f1, n2h, f2;
+                    two_sum(p0, p1, s1, f1);
+                    two_sum(s1, p2, n2h, f2);
+                    T n2l = f1 + f2 + e0 + e1 + e2 + T(2) * (h[0] * l[0] + h[1] * l[1] + h[2] * l[2]);
+                    T nh, nl;
+                    fast_two_sum(n2h, n2l, nh, nl);
+                    if (!(nh > T(0)) || !isfinite(nh)) {
+                        atomicOr(d.status, 1);
+                        nh = T(1);
+                        nl = T(0);
+                    }
+                    const T r0 = rsqrt(nh);
+                    T q, qe, a, ae;
+                    two_prod(r0, r0, q, qe);
+                    two_prod(nh, q, a, ae);
+                    const T rho = ((T(1) - a) - ae) - (nh * qe + nl * q);
+                    const T cc = T(0.5) * r0 * rho;                  // 1/|m***| = r0 + cc
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        T pp, pe;
+                        two_prod(h[i], r0, pp, pe);
+                        T oh, ol;
+                        fast_two_sum(pp, pe + (h[i] * cc + l[i] * r0), oh, ol);
+                        d.field[pg.fin_out[i]][c] = oh;
+                        d.flo[pg.fin_out[i]][c] = ol;
+                        slabs[i * S + idx] = oh;
+                        if (pg.fin_v[i] >= 0) d.field[pg.fin_v[i]][c] = h[i] + l[i];
+                    }
+                    continue;
                 }
-            }
-            __syncthreads();
-        } else {
-            dct3_lines<T>(s, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
-        }
-        PHASE_MARK(7);
-        dct3_lines<T, NX>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
-        PHASE_MARK(8);
-        if (pg.inv_store[i] >= 0) {
-            T* out = d.field[pg.inv_store[i]];
-            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                int z = idx / nx, x = idx - z * nx;
-                out[cell_of(z, x)] = s[idx];
-            }
-        }
-    }
-
-    PHASE_MARK(9);
-    // ---- phase U: pointwise updates ----------------------------------------------------------
-    if (pg.op == 1) {
-        // Gauss-Seidel cross product: out = base + p*q - r*s  (delta form, see host program)
-        T* out = d.field[pg.gs_out];
-        T* outl = d.flo[pg.gs_out];
-        T* res = slabs + 2 * S;
-        const T* bl_ = pg.gs_base >= 0 ? d.flo[pg.gs_base] : nullptr;
-        const T* ql_ = pg.gs_q >= 0 ? d.flo[pg.gs_q] : nullptr;
-        const T* sl_ = pg.gs_s >= 0 ? d.flo[pg.gs_s] : nullptr;
-        constexpr int kB = sizeof(T) == 4 ? 4 : 2;
-        for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
-            T bb[kB], pp[kB], qq[kB], rr[kB], ss[kB], bl[kB], ql[kB], sl[kB];
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int idx = i0 + u * blockDim.x;
-                if (idx >= nxz) break;
-                const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
-                bb[u] = load_ref(d, pg.gs_base, c, slabs, S, idx);
-                pp[u] = load_ref(d, pg.gs_p, c, slabs, S, idx);
-                qq[u] = load_ref(d, pg.gs_q, c, slabs, S, idx);
-                rr[u] = load_ref(d, pg.gs_r, c, slabs, S, idx);
-                ss[u] = load_ref(d, pg.gs_s, c, slabs, S, idx);
-                bl[u] = bl_ ? bl_[c] : T(0);
-                ql[u] = ql_ ? ql_[c] : T(0);
-                sl[u] = sl_ ? sl_[c] : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int idx = i0 + u * blockDim.x;
-                if (idx >= nxz) break;
-                const long long c = cell_of(idx / nx, idx - (idx / nx) * nx);
-                if (outl) {
-                    // double-float state: base (hi, lo) + increment p (q_hi + q_lo) - r (s_hi + s_lo)
-                    const T rs = fma(rr[u], sl[u], rr[u] * ss[u]);
-                    const T inc = fma(pp[u], qq[u], fma(pp[u], ql[u], -rs));
-                    T hi, e;
-                    two_sum(bb[u], inc, hi, e);
-                    T h2, l2;
-                    fast_two_sum(hi, e + bl[u], h2, l2);
-                    out[c] = h2;
-                    outl[c] = l2;
-                    res[idx] = h2;
-                } else {
-                    const T v = bb[u] + (pp[u] * qq[u] - rr[u] * ss[u]);
-                    out[c] = v;
-                    res[idx] = v;
-                }
-            }
-        }
-        __syncthreads();
-    } else if (pg.op == 2) {
-        // Step 2 + Step 3: m*** = m** + delta (+ dt f_e), m^{n+1} = m*** / |m***|
-        const double tnow = F.t0 + (double)(*d.step_ctr) * F.dt;
-        const bool dfl = d.flo[pg.fin_out[0]] != nullptr;
-        for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-            int z = idx / nx, x = idx - z * nx;
-            long long c = cell_of(z, x);
-            if (dfl) {
-                // m*** = m** + delta in double-float, then |m***|^-1 by one double-float Newton step
-                T h[3], l[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    T s1, e1;
-                    two_sum(d.field[pg.fin_in[i]][c], slabs[i * S + idx], s1, e1);
-                    fast_two_sum(s1, e1 + d.flo[pg.fin_in[i]][c], h[i], l[i]);
-                }
+                T v[3];
+    #pragma unroll
+                for (int i = 0; i < 3; ++i) v[i] = d.field[pg.fin_in[i]][c] + slabs[i * S + idx];
                 if (F.forcing) {
                     double fe[3];
                     mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        double v = (double)h[i] + (double)l[i] + F.dt * fe[i];
-                        h[i] = (T)v;
-                        l[i] = (T)(v - (double)h[i]);
-                    }
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i) v[i] += T(F.dt * fe[i]);
                 }
-                T p0, e0, p1, e1, p2, e2;
-                two_prod(h[0], h[0], p0, e0);
-                two_prod(h[1], h[1], p1, e1);
-                two_prod(h[2], h[2], p2, e2);
-                T s1, f1, n2h, f2;
-                two_sum(p0, p1, s1, f1);
-                two_sum(s1, p2, n2h, f2);
-                T n2l = f1 + f2 + e0 + e1 + e2 + T(2) * (h[0] * l[0] + h[1] * l[1] + h[2] * l[2]);
-                T nh, nl;
-                fast_two_sum(n2h, n2l, nh, nl);
-                if (!(nh > T(0)) || !isfinite(nh)) {
+                T n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                if (!(n2 > T(0)) || !isfinite(n2)) {
                     atomicOr(d.status, 1);
-                    nh = T(1);
-                    nl = T(0);
+                    n2 = T(1);
                 }
-                const T r0 = rsqrt(nh);
-                T q, qe, a, ae;
-                two_prod(r0, r0, q, qe);
-                two_prod(nh, q, a, ae);
-                const T rho = ((T(1) - a) - ae) - (nh * qe + nl * q);
-                const T cc = T(0.5) * r0 * rho;                  // 1/|m***| = r0 + cc
-#pragma unroll
+                T inv = T(1) / sqrt(n2);
+    #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    T pp, pe;
-                    two_prod(h[i], r0, pp, pe);
-                    T oh, ol;
-                    fast_two_sum(pp, pe + (h[i] * cc + l[i] * r0), oh, ol);
-                    d.field[pg.fin_out[i]][c] = oh;
-                    d.flo[pg.fin_out[i]][c] = ol;
-                    slabs[i * S + idx] = oh;
-                    if (pg.fin_v[i] >= 0) d.field[pg.fin_v[i]][c] = h[i] + l[i];
+                    T w = v[i] * inv;
+                    d.field[pg.fin_out[i]][c] = w;
+                    slabs[i * S + idx] = w;
+                    if (pg.fin_v[i] >= 0) d.field[pg.fin_v[i]][c] = v[i];
                 }
-                continue;
             }
-            T v[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) v[i] = d.field[pg.fin_in[i]][c] + slabs[i * S + idx];
-            if (F.forcing) {
-                double fe[3];
-                mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) v[i] += T(F.dt * fe[i]);
-            }
-            T n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-            if (!(n2 > T(0)) || !isfinite(n2)) {
-                atomicOr(d.status, 1);
-                n2 = T(1);
-            }
-            T inv = T(1) / sqrt(n2);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                T w = v[i] * inv;
-                d.field[pg.fin_out[i]][c] = w;
-                slabs[i * S + idx] = w;
-                if (pg.fin_v[i] >= 0) d.field[pg.fin_v[i]][c] = v[i];
-            }
+            __syncthreads();
         }
-        __syncthreads();
-    }
 
-    PHASE_MARK(10);
-    // ---- phase F: forward zero-padded FFT (x R2C, z C2C) -> spectral slots ---------------------
-    if (stray) {
-        for (int i = 0; i < pg.n_fwd; ++i) {
-            const int ref = pg.fwd_src[i];
-            const T* src;
-            if (ref >= 0) {
-                T* s0 = slabs;
-                const T* in = d.field[ref];
-                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                    int z = idx / nx, x = idx - z * nx;
-                    s0[idx] = in[cell_of(z, x)];
+        PHASE_MARK(10);
+        // ---- phase F: forward zero-padded FFT (x R2C, z C2C) -> spectral slots ---------------------
+        if (stray) {
+            for (int i = 0; i < pg.n_fwd; ++i) {
+                const int ref = pg.fwd_src[i];
+                const T* src;
+                if (ref >= 0) {
+                    T* s0 = slabs;
+                    const T* in = d.field[ref];
+                    for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                        int z = idx / nx, x = idx - z * nx;
+                        s0[idx] = in[cell_of(z, x)];
+                    }
+                    __syncthreads();
+                    src = s0;
+                } else {
+                    src = slabs + (-1 - ref) * S;
                 }
-                __syncthreads();
-                src = s0;
-            } else {
-                src = slabs + (-1 - ref) * S;
-            }
-            PHASE_MARK(11);
-            V* r = r2c_lines<T, 2 * NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
-            PHASE_MARK(12);
-            V* out = d.spec[pg.fwd_dst[i]] + sbase;
-            if (zreg) {
-                // zero-padded DFT along z in registers, one thread per kx column
-                for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
-                    V v[2 * kZReg];
-#pragma unroll
-                    for (int z = 0; z < 2 * kZReg; ++z) v[z] = z < nz ? r2c_get<T>(r, z, kx, Px) : cmk<V>(T(0), T(0));
-                    if (zfft_reg<T, false>(v, Pz)) {
-#pragma unroll
-                        for (int kz = 0; kz < 2 * kZReg; ++kz)
-                            if (kz < Pz) out[((long long)kz * ny + y) * Kx + kx] = v[kz];
-                    } else {
-                        for (int kz = 0; kz < Pz; ++kz) {
-                            V acc = cmk<V>(T(0), T(0));
-                            int m = 0;
-#pragma unroll
-                            for (int z = 0; z < kZReg; ++z) {
-                                if (z < nz) acc = cadd(acc, cmul(v[z], twz[m]));
-                                m += kz;
-                                if (m >= Pz) m -= Pz;
+                PHASE_MARK(11);
+                V* r = r2c_lines<T, 2 * NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
+                PHASE_MARK(12);
+                V* out = d.spec[pg.fwd_dst[i]] + sbase;
+                if (zreg) {
+                    // zero-padded DFT along z in registers, one thread per kx column
+                    for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
+                        V v[2 * kZReg];
+    #pragma unroll
+                        for (int z = 0; z < 2 * kZReg; ++z) v[z] = z < nz ? r2c_get<T>(r, z, kx, Px) : cmk<V>(T(0), T(0));
+                        if (zfft_reg<T, false>(v, Pz)) {
+    #pragma unroll
+                            for (int kz = 0; kz < 2 * kZReg; ++kz)
+                                if (kz < Pz) out[((long long)kz * ny + y) * Kx + kx] = v[kz];
+                        } else {
+                            for (int kz = 0; kz < Pz; ++kz) {
+                                V acc = cmk<V>(T(0), T(0));
+                                int m = 0;
+    #pragma unroll
+                                for (int z = 0; z < kZReg; ++z) {
+                                    if (z < nz) acc = cadd(acc, cmul(v[z], twz[m]));
+                                    m += kz;
+                                    if (m >= Pz) m -= Pz;
+                                }
+                                out[((long long)kz * ny + y) * Kx + kx] = acc;
                             }
-                            out[((long long)kz * ny + y) * Kx + kx] = acc;
                         }
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
-            }
-            for (int kc0 = 0; !zreg && kc0 < Kx; kc0 += KC) {
-                const int kcn = min(KC, Kx - kc0);
-                for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
-                    int z = idx / kcn, kc = idx - z * kcn;
-                    zw0[z * KC + kc] = (z < nz) ? r2c_get<T>(r, z, kc0 + kc, Px) : cmk<V>(T(0), T(0));
+                for (int kc0 = 0; !zreg && kc0 < Kx; kc0 += KC) {
+                    const int kcn = min(KC, Kx - kc0);
+                    for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
+                        int z = idx / kcn, kc = idx - z * kcn;
+                        zw0[z * KC + kc] = (z < nz) ? r2c_get<T>(r, z, kc0 + kc, Px) : cmk<V>(T(0), T(0));
+                    }
+                    __syncthreads();
+                    V* q = fft_lines<T, false>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
+                    for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
+                        int kz = idx / kcn, kc = idx - kz * kcn;
+                        out[((long long)kz * ny + y) * Kx + kc0 + kc] = q[kz * KC + kc];
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
-                V* q = fft_lines<T, false>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
-                for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
-                    int kz = idx / kcn, kc = idx - kz * kcn;
-                    out[((long long)kz * ny + y) * Kx + kc0 + kc] = q[kz * KC + kc];
-                }
-                __syncthreads();
             }
         }
+        PHASE_MARK(13);
+        if constexpr (MULTI) __syncthreads();   // the next row reuses every shared buffer
     }
-    PHASE_MARK(13);
     if constexpr (ZTC) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();

@@ -49,6 +49,10 @@ def lib():
     L.sgspm_create_batch.argtypes = [i, ctypes.POINTER(Grid), dp, dp, dp, dp, dp, i, vp, ctypes.POINTER(vp)]
     L.sgspm_set_applied_field.argtypes = [vp, dp]
     L.sgspm_set_alpha.argtypes = [vp, dp]
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.sgspm_xz_classes.argtypes = [vp, ip, ip, i]
+    L.sgspm_set_packing.argtypes = [vp, ip, i]
+    L.sgspm_autotune.argtypes = [vp, i, ip, i]
     L.sgspm_set_field.argtypes = [vp, i, vp, i]
     L.sgspm_get_field.argtypes = [vp, i, vp, i]
     L.sgspm_step.argtypes = [vp, ll]
@@ -71,7 +75,8 @@ def lib():
     L.sgspm_energy_noalloc.restype = ctypes.c_int
     L.sgspm_noalloc_last_error.argtypes = []
     L.sgspm_noalloc_last_error.restype = ctypes.c_char_p
-    for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_alpha", "sgspm_set_field",
+    for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_alpha", "sgspm_xz_classes", "sgspm_set_packing", "sgspm_autotune",
+                 "sgspm_set_field",
                  "sgspm_get_field", "sgspm_step", "sgspm_energy", "sgspm_set_forcing", "sgspm_set_time",
                  "sgspm_get_time", "sgspm_sync", "sgspm_destroy", "sgspm_launches_per_step", "sgspm_version",
                  "sgspm_profile_step"):
@@ -197,6 +202,29 @@ class Handle:
         self._check(lib().sgspm_set_alpha(self.h, _dptr(a)))
         for f, v in zip(self.films, a):
             f["alpha"] = float(v)
+
+    # ---- batch packing ------------------------------------------------------------------------
+    def xz_classes(self):
+        """[(key, rows per CTA)] of the slab-pass size classes (key = nx, or 0: runtime length)."""
+        n = lib().sgspm_xz_classes(self.h, None, None, 0)
+        if n < 0:
+            self._check(n)
+        keys, rows = (ctypes.c_int * max(n, 1))(), (ctypes.c_int * max(n, 1))()
+        self._check(min(0, lib().sgspm_xz_classes(self.h, keys, rows, n)))
+        return [(keys[c], rows[c]) for c in range(n)]
+
+    def set_packing(self, rows):
+        r = (ctypes.c_int * len(rows))(*[int(v) for v in rows])
+        self._check(lib().sgspm_set_packing(self.h, r, len(rows)))
+
+    def autotune(self, steps=3):
+        """Choose rows per CTA of every packable size class by timing; returns the choice."""
+        n = len(self.xz_classes())
+        out = (ctypes.c_int * max(n, 1))()
+        rc = lib().sgspm_autotune(self.h, int(steps), out, n)
+        if rc < 0:
+            self._check(rc)
+        return [out[c] for c in range(n)]
 
     def set_field(self, which, x):
         p, code, keep = _buffer(x)

@@ -52,3 +52,30 @@ def test_ensemble256_spot_films_match_oracle(ensemble, fp64, tol):
     # every film of the batch still has unit-length magnetisation
     for m in got:
         assert np.abs(np.sqrt((m * m).sum(axis=0)) - 1).max() < (1e-13 if fp64 else 1e-6)
+
+
+def test_packing_and_autotune_leave_results_unchanged():
+    """Packing several y rows per slab CTA is a launch-shape choice: results are bitwise the same
+    for every packing, and the autotuner restores m (and the step count) after its timing runs."""
+    films = [dict(n=(64, 16, 2), h=(1 / 64,) * 3, eps=0.016, Q=6.2e-4, alpha=0.01, dt=0.01, he=(0.02, 0, 0)),
+             dict(n=(96, 12, 2), h=(1 / 96,) * 3, eps=0.016, Q=6.2e-4, alpha=0.002, dt=0.01, he=(-0.01, 0, 0)),
+             dict(n=(128, 8, 4), h=(1 / 128,) * 3, eps=0.016, Q=6.2e-4, alpha=0.03, dt=0.01, he=(0.0, 0.01, 0))]
+    m0 = np.concatenate([inputs.random_unit(60 + i, f["n"]).reshape(-1) for i, f in enumerate(films)])
+
+    def run(setup):
+        H = sgspm.Handle(films)
+        H.set_m(m0)
+        info = setup(H)
+        H.step(6)
+        m = H.get_m()
+        H.close()
+        return m, info
+
+    base, cls = run(lambda H: H.xz_classes())
+    assert all(r == 1 for _, r in cls)
+    for rows in (2, 4, 8):
+        got, _ = run(lambda H: H.set_packing([rows] * len(cls)))
+        assert np.array_equal(got, base), rows
+    tuned, choice = run(lambda H: H.autotune(2))
+    assert np.array_equal(tuned, base)
+    assert len(choice) == len(cls) and all(r in (1, 2, 4, 8) for r in choice)
