@@ -275,12 +275,16 @@ static cudaError_t attr_xz(int key, size_t smem, bool tf32x3) {
             } else if (key == 128) {
                 e = cudaFuncSetAttribute(xz_kernel<T, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             } else {
-                // shared by several classes (runtime x length): allow the device's opt-in maximum
+                // shared by several classes (runtime x length): allow the most dynamic shared
+                // memory the device gives this kernel (opt-in maximum less its static part)
                 int dev = 0, mx = 0;
                 cudaGetDevice(&dev);
                 cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+                cudaFuncAttributes fa;
+                e = cudaFuncGetAttributes(&fa, xz_kernel<T, 0, false, true>);
+                if (e != cudaSuccess) return e;
                 e = cudaFuncSetAttribute(xz_kernel<T, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         std::max(mx, (int)smem));
+                                         std::max(mx - (int)fa.sharedSizeBytes, (int)smem));
             }
             if (e != cudaSuccess) return e;
         }
