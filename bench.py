@@ -152,6 +152,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands (cold
+# caches; profiles/passes_film256x256x8_fp32.md).  Only valid for the kernel that was captured:
+# set an entry back to None when its kernel changes.
+NCU_TRAFFIC = {1: 17.2e6}   # slab pass, right-hand-side launch (kind 1), 256x256x8 FP32
+
+
 # algorithmic bytes per cell of each launch kind, FP32 (field crossings x 4 B; see the design notes)
 def algorithmic_bytes_per_cell(kind, ncomp=1):
     k, v = divmod(kind, 10)
@@ -315,7 +321,9 @@ def run_gpu(args):
         roof = {"bound": "hbm", "kernel": f"{kinds[dom_type]} (launch kind {dom_kind})", "achieved": achieved,
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": bpc * ncell, "launch_ms": dom_ms,
-                "kernel_share_of_step": per_type[dom_type] / total, "traffic": None}
+                "kernel_share_of_step": per_type[dom_type] / total,
+                "traffic": NCU_TRAFFIC.get(dom_kind) if args.form == "fp32" else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write, cold caches)"}
     # whole-step algorithmic fraction (292 B per cell-step, FP32)
     step_frac = 292.0 * value / world / (hbm * 1e9) if hbm else None
 
