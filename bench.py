@@ -248,6 +248,68 @@ def run_strip(sgspm, torch, stream, steps, tf32x3=True):
             "l2": "not flushed (working set in L2)"}
 
 
+def run_small_configs(sgspm, torch, stream):
+    """The 32x32x4 FP64 film (200 steps, against the oracle) and the 128x128x4 adjoint (500
+    recorded steps with checkpoints every 50, then the reverse sweep), timed with CUDA events."""
+    out = {}
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    w = inputs.WORKLOADS["film32x32x4_fp64"]
+    m0 = inputs.initial_state(w)
+    H = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=True,
+                   stream=stream.cuda_stream)
+    H.set_m(m0)
+    H.step(3)
+    H.set_m(m0)
+    a, b = ev()
+    a.record(stream)
+    H.step(w["steps"])
+    b.record(stream)
+    H.sync()
+    ms = a.elapsed_time(b)
+    got = H.split(H.get_m())[0]
+    H.close()
+    from oracle import scheme
+    o = scheme.Oracle(scheme.Params(n=w["n"], h=w["h"], eps=w["eps"], Q=w["Q"], alpha=w["alpha"], dt=w["dt"],
+                                    u=w["u"], he=w["he"]))
+    m = m0.copy()
+    t0 = time.perf_counter()
+    for _ in range(w["steps"]):
+        m = o.step(m, 0.0)
+    cpu_s = time.perf_counter() - t0
+    nc = int(np.prod(w["n"]))
+    out["film32x32x4_fp64"] = {"steps": w["steps"], "ms_per_step": ms / w["steps"],
+                               "value": nc * w["steps"] / (ms / 1e3), "unit": UNIT,
+                               "max_abs_dm_vs_oracle": float(np.abs(got - m).max()),
+                               "oracle_cpu_value": nc * w["steps"] / cpu_s, "oracle_cpu_cores": os.cpu_count()}
+    w = inputs.WORKLOADS["film128x128x4_adjoint"]
+    m0 = inputs.initial_state(w)
+    n = w["n"]
+    nc = int(np.prod(n))
+    he = 0.01 * np.random.default_rng(3).normal(size=3 * nc)
+    H = sgspm.film(n, w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], fp64=False, stream=stream.cuda_stream)
+    H.set_m(m0)
+    H.set_he(he)
+    a, b = ev()
+    a.record(stream)
+    H.record(w["steps"], 50)
+    b.record(stream)
+    H.sync()
+    fwd_ms = a.elapsed_time(b)
+    mT = H.get_m().reshape(3, -1)
+    g = np.zeros_like(mT)
+    g[0] = 2.0 * (mT[0] - 1.0) / nc
+    a.record(stream)
+    H.grad(g.reshape(-1))
+    b.record(stream)
+    H.sync()
+    bwd_ms = a.elapsed_time(b)
+    H.close()
+    out["film128x128x4_adjoint"] = {"steps": w["steps"], "checkpoint_every": 50, "dtype": "f32",
+                                    "record_ms": fwd_ms, "grad_ms": bwd_ms,
+                                    "value": nc * w["steps"] / ((fwd_ms + bwd_ms) / 1e3), "unit": UNIT + " (forward + reverse)"}
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as tdist
@@ -383,6 +445,7 @@ def run_gpu(args):
     launches = args.steps * H.launches_per_step()
     H.close()
     ens = run_ensemble(sgspm, torch, stream, args.ensemble_steps) if args.ensemble_steps > 0 else None
+    small = run_small_configs(sgspm, torch, stream) if args.small_configs else None
     strip = None
     if args.strip_steps > 0:
         strip = run_strip(sgspm, torch, stream, args.strip_steps, tf32x3=True)
@@ -410,6 +473,7 @@ def run_gpu(args):
                         "path": "sgspm_set_field(pinned host f32) + sgspm_step(1) + sgspm_get_field(pinned host f32)"},
                 "gpu_launches": launches,
                 "ensemble": ens,
+                "small_configs": small,
                 "strip": strip,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
@@ -426,6 +490,8 @@ def main():
     ap.add_argument("--form", default="fp32", choices=["fp32", "tf32x3"],
                     help="form of the timed film: FP32 (default) or TF32X3 (z DCTs on the tensor cores)")
     ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps for cpu_baseline (0: skip)")
+    ap.add_argument("--small-configs", type=int, default=1,
+                    help="also time the 32x32x4 FP64 film and the 128x128x4 adjoint (0: skip)")
     ap.add_argument("--strip-steps", type=int, default=400,
                     help="timed steps of the 512x64x4 Neel-wall strip, reported beside the line (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=20,
