@@ -327,6 +327,7 @@ def run_gpu(args):
                    stream=stream.cuda_stream, tf32x3=(args.form == "tf32x3"))
     m0_t = torch.from_numpy(m0.astype(np.float32).reshape(-1)).cuda()
     H.set_m(m0_t)
+    tuned = {"slab_rows_per_cta": H.autotune(3), "heat_lines_per_cta": H.heat_tile()} if args.autotune else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     H.step(args.warmup)
     H.sync()
@@ -459,7 +460,8 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": list(w["n"]), "h": w["h"][0], "eps": w["eps"], "Q": w["Q"],
                            "alpha": w["alpha"], "dt": w["dt"], "he": list(w["he"]), "stray": True,
-                           "parallelism": f"replicas{world}", "l2": "flushed before every timed step (256 MiB write)"},
+                           "parallelism": f"replicas{world}", "l2": "flushed before every timed step (256 MiB write)",
+                           "autotuned": tuned},
                 "roofline": roof,
                 "step_algorithmic_hbm_frac": step_frac,
                 "fp64_form": {"ms_per_step": fp64_ms, "value": ncell / (fp64_ms / 1e3), "unit": UNIT},
@@ -490,6 +492,8 @@ def main():
     ap.add_argument("--form", default="fp32", choices=["fp32", "tf32x3"],
                     help="form of the timed film: FP32 (default) or TF32X3 (z DCTs on the tensor cores)")
     ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps for cpu_baseline (0: skip)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="choose launch shapes of the timed film with sgspm_autotune before timing (0: defaults)")
     ap.add_argument("--small-configs", type=int, default=1,
                     help="also time the 32x32x4 FP64 film and the 128x128x4 adjoint (0: skip)")
     ap.add_argument("--strip-steps", type=int, default=400,

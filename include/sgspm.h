@@ -120,11 +120,16 @@ int sgspm_set_applied_field(sgspm_t h, const double* he);
  * sgspm_set_packing: rows per CTA (1..8), one entry per class; ERR_UNSUPPORTED for > 1 on a
  *   class that runs one row per CTA.  Results do not depend on the packing (bitwise).
  * sgspm_autotune: times `steps` steps for rows 1, 2, 4, 8 of every packable class and keeps the
- *   fastest; m and the step count are restored afterwards (it allocates a copy of m while it
+ *   fastest, then the heat tile (below) the same way; m and the step count are restored afterwards (it allocates a copy of m while it
  *   runs).  Needs m set (ERR_STATE).  Writes the chosen rows to rows_out (cap entries) when
  *   non-NULL and returns the number of classes.
  */
 int sgspm_xz_classes(sgspm_t h, int* keys, int* rows, int cap);
+/* y heat pass: x lines per CTA (1..16; default 8).  sgspm_heat_tile returns the current value;
+ * sgspm_set_heat_tile: ERR_ARG outside 1..16, ERR_UNSUPPORTED if the tile does not fit in shared
+ * memory.  sgspm_autotune also chooses it (from 4, 6, 8, 12, 16).  Results do not depend on it. */
+int sgspm_heat_tile(sgspm_t h);
+int sgspm_set_heat_tile(sgspm_t h, int tx);
 int sgspm_set_packing(sgspm_t h, const int* rows, int n);
 int sgspm_autotune(sgspm_t h, int steps, int* rows_out, int cap);
 

@@ -105,6 +105,7 @@ struct sgspm_ctx {
     int n_ys[4] = {};
     int tx_s[4] = {};
     size_t smem_xz = 0, smem_yh = 0, smem_ys[4] = {};
+    size_t smem_max = 0;               // opt-in shared memory per block of the device
     bool warp_stray = false;           // register-resident stray line pass (all Py in 64..512)
     int4* d_work_yw = nullptr;
     int n_yw = 0;
@@ -1048,6 +1049,40 @@ static int newell_setup(sgspm_ctx* ctx, const Film& F) {
     return SGSPM_OK;
 }
 
+// y heat pass: shared memory of a CTA of tx lines of length ny
+template <typename T>
+static size_t heat_smem(int ny, int tx) {
+    const size_t V = sizeof(cplx<T>);
+    return (size_t)2 * ny * V + (size_t)2 * ((tx + 1) / 2) * ny * V + (size_t)tx * (ny + 8) * sizeof(T);
+}
+
+// (Re)build the y heat pass's size classes with tx x lines per CTA (a tuning knob).
+template <typename T>
+static int build_heat_classes(sgspm_ctx* ctx, int tx) {
+    std::map<int, std::vector<int4>> wy;
+    std::map<int, size_t> syk;
+    for (int f = 0; f < ctx->nfilm; ++f) {
+        const Film& F = ctx->films[f];
+        const int ky = sizeof(T) == 8 ? 0 : pow2_key(F.ny, 8, 512);
+        for (int kz = 0; kz < F.nz; ++kz)
+            for (int x0 = 0; x0 < F.nx; x0 += tx) wy[ky].push_back(make_int4(f, kz, x0, std::min(tx, F.nx - x0)));
+        syk[ky] = std::max(syk[ky], heat_smem<T>(F.ny, tx));
+    }
+    if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& c : ctx->yh_cls) cudaFree(c.work);
+    ctx->yh_cls.clear();
+    for (auto& kv : wy) {
+        sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), syk[kv.first]};
+        CK(cudaMalloc(&c.work, std::max<size_t>(1, kv.second.size()) * sizeof(int4)));
+        CK(cudaMemcpy(c.work, kv.second.data(), kv.second.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CK(attr_yh<T>(c.key, c.smem));
+        ctx->yh_cls.push_back(c);
+    }
+    ctx->tx_h = tx;
+    drop_graph(ctx);
+    return SGSPM_OK;
+}
+
 template <typename T>
 static int setup_t(sgspm_ctx* ctx) {
     const size_t V = sizeof(cplx<T>);
@@ -1140,6 +1175,7 @@ static int setup_t(sgspm_ctx* ctx) {
     CK(cudaGetDevice(&dev));
     int smem_max = 0;
     CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    ctx->smem_max = (size_t)smem_max;
     size_t sx = 0, sy = 0;
     int maxPy = 1, maxny = 1;
     for (const Film& F : ctx->films) {
@@ -1178,18 +1214,14 @@ static int setup_t(sgspm_ctx* ctx) {
     };
     int rc;
     {
-        std::map<int, std::vector<int4>> wx, wy;
-        std::map<int, size_t> sxk, syk;
+        std::map<int, std::vector<int4>> wx;
+        std::map<int, size_t> sxk;
         for (int f = 0; f < ctx->nfilm; ++f) {
             const Film& F = ctx->films[f];
-            const int kx = sizeof(T) == 8 ? 0 : pow2_key(F.nx, 8, 512), ky = sizeof(T) == 8 ? 0 : pow2_key(F.ny, 8, 512);
+            const int kx = sizeof(T) == 8 ? 0 : pow2_key(F.nx, 8, 512);
             for (int y = 0; y < F.ny; ++y) wx[kx].push_back(make_int4(f, y, 0, 0));
-            for (int kz = 0; kz < F.nz; ++kz)
-                for (int x0 = 0; x0 < F.nx; x0 += ctx->tx_h) wy[ky].push_back(make_int4(f, kz, x0, std::min(ctx->tx_h, F.nx - x0)));
             XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray, ztc_class(ctx->tf32x3, kx));
             sxk[kx] = std::max(sxk[kx], xz_smem_bytes<T>(L));
-            syk[ky] = std::max(syk[ky], (size_t)2 * F.ny * V + (size_t)2 * ((ctx->tx_h + 1) / 2) * F.ny * V +
-                                            (size_t)ctx->tx_h * (F.ny + 8) * sizeof(T));
             first_e.push_back((int)we.size());
             long long nc = (long long)F.nx * F.ny * F.nz;
             for (long long c0 = 0; c0 < nc; c0 += 4096) we.push_back(make_int4(f, (int)c0, (int)std::min(4096LL, nc - c0), 0));
@@ -1200,13 +1232,8 @@ static int setup_t(sgspm_ctx* ctx) {
             CK(attr_xz<T>(c.key, c.smem, ctx->tf32x3));
             ctx->xz_cls.push_back(c);
         }
-        for (auto& kv : wy) {
-            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), syk[kv.first]};
-            if ((rc = up4(&c.work, kv.second))) return rc;
-            CK(attr_yh<T>(c.key, c.smem));
-            ctx->yh_cls.push_back(c);
-        }
     }
+    if ((rc = build_heat_classes<T>(ctx, ctx->tx_h))) return rc;
     first_e.push_back((int)we.size());
     if ((rc = up4(&ctx->d_work_e, we))) return rc;
     ctx->n_e = (int)we.size();
@@ -1720,6 +1747,18 @@ static int set_class_rows(sgspm_ctx* ctx, size_t c, int rows) {
     return SGSPM_OK;
 }
 
+int sgspm_heat_tile(sgspm_t ctx) { return ctx ? ctx->tx_h : SGSPM_ERR_ARG; }
+
+int sgspm_set_heat_tile(sgspm_t ctx, int tx) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (tx < 1 || tx > 16) return fail(ctx, SGSPM_ERR_ARG, "x lines per heat CTA must be in 1..16");
+    int maxny = 1;
+    for (const Film& F : ctx->films) maxny = std::max(maxny, F.ny);
+    if ((ctx->fp64 ? heat_smem<double>(maxny, tx) : heat_smem<float>(maxny, tx)) > ctx->smem_max)
+        return fail(ctx, SGSPM_ERR_UNSUPPORTED, "heat tile does not fit in shared memory");
+    return ctx->fp64 ? build_heat_classes<double>(ctx, tx) : build_heat_classes<float>(ctx, tx);
+}
+
 int sgspm_xz_classes(sgspm_t ctx, int* keys, int* rows, int cap) {
     if (!ctx) return SGSPM_ERR_ARG;
     const int n = (int)ctx->xz_cls.size();
@@ -1793,6 +1832,32 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
             }
         }
         if (!rc) rc = set_class_rows(ctx, (size_t)c, best_rows);
+    }
+    // y heat pass: x lines per CTA
+    if (!rc) {
+        int maxny = 1;
+        for (const Film& F : ctx->films) maxny = std::max(maxny, F.ny);
+        float best = 1e30f;
+        int best_tx = ctx->tx_h;
+        for (int tx : {4, 6, 8, 12, 16}) {
+            const size_t sm = ctx->fp64 ? heat_smem<double>(maxny, tx) : heat_smem<float>(maxny, tx);
+            if (sm > ctx->smem_max) continue;
+            if ((rc = ctx->fp64 ? build_heat_classes<double>(ctx, tx) : build_heat_classes<float>(ctx, tx))) break;
+            if ((rc = sgspm_step(ctx, 1))) break;
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = SGSPM_ERR_CUDA; break; }
+            if ((rc = sgspm_step(ctx, steps))) break;
+            if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = SGSPM_ERR_CUDA;
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_tx = tx;
+            }
+        }
+        if (!rc) rc = ctx->fp64 ? build_heat_classes<double>(ctx, best_tx) : build_heat_classes<float>(ctx, best_tx);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

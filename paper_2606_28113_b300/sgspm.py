@@ -53,6 +53,8 @@ def lib():
     L.sgspm_xz_classes.argtypes = [vp, ip, ip, i]
     L.sgspm_set_packing.argtypes = [vp, ip, i]
     L.sgspm_autotune.argtypes = [vp, i, ip, i]
+    L.sgspm_heat_tile.argtypes = [vp]
+    L.sgspm_set_heat_tile.argtypes = [vp, i]
     L.sgspm_set_field.argtypes = [vp, i, vp, i]
     L.sgspm_get_field.argtypes = [vp, i, vp, i]
     L.sgspm_step.argtypes = [vp, ll]
@@ -76,6 +78,7 @@ def lib():
     L.sgspm_noalloc_last_error.argtypes = []
     L.sgspm_noalloc_last_error.restype = ctypes.c_char_p
     for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_alpha", "sgspm_xz_classes", "sgspm_set_packing", "sgspm_autotune",
+                 "sgspm_heat_tile", "sgspm_set_heat_tile",
                  "sgspm_set_field",
                  "sgspm_get_field", "sgspm_step", "sgspm_energy", "sgspm_set_forcing", "sgspm_set_time",
                  "sgspm_get_time", "sgspm_sync", "sgspm_destroy", "sgspm_launches_per_step", "sgspm_version",
@@ -216,6 +219,16 @@ class Handle:
     def set_packing(self, rows):
         r = (ctypes.c_int * len(rows))(*[int(v) for v in rows])
         self._check(lib().sgspm_set_packing(self.h, r, len(rows)))
+
+    def heat_tile(self):
+        """x lines per CTA of the y heat pass."""
+        rc = lib().sgspm_heat_tile(self.h)
+        if rc < 0:
+            self._check(rc)
+        return rc
+
+    def set_heat_tile(self, tx):
+        self._check(lib().sgspm_set_heat_tile(self.h, int(tx)))
 
     def autotune(self, steps=3):
         """Choose rows per CTA of every packable size class by timing; returns the choice."""

@@ -76,6 +76,9 @@ def test_packing_and_autotune_leave_results_unchanged():
     for rows in (2, 4, 8):
         got, _ = run(lambda H: H.set_packing([rows] * len(cls)))
         assert np.array_equal(got, base), rows
+    for tx in (4, 6, 16):
+        got, _ = run(lambda H: H.set_heat_tile(tx))
+        assert np.array_equal(got, base), tx
     tuned, choice = run(lambda H: H.autotune(2))
     assert np.array_equal(tuned, base)
     assert len(choice) == len(cls) and all(r in (1, 2, 4, 8) for r in choice)
