@@ -331,7 +331,7 @@ static cudaError_t attr_yh(int key, size_t smem) {
 template <typename T, int NOUT>
 static void launch_yw_n(int key, int nb, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
     const unsigned nt = 32 * kWarpLines;
-    const size_t smem = yw_smem_bytes<T>(32 * key, NOUT, pg.in_mask, pg.fresh_mask);
+    const size_t smem = yw_smem_bytes<T>(32 * key, NOUT);
     switch (key) {
         case 2: launch_pdl(y_stray_warp_kernel<T, NOUT, 2>, nb, nt, smem, st, d, w, pg); break;
         case 4: launch_pdl(y_stray_warp_kernel<T, NOUT, 4>, nb, nt, smem, st, d, w, pg); break;
@@ -1250,7 +1250,7 @@ static int setup_t(sgspm_ctx* ctx) {
     // register-resident stray pass when every film's padded y length is 64..512, per length class
     ctx->warp_stray = ctx->stray;
     for (const Film& F : ctx->films)
-        if (!(F.Py == 64 || F.Py == 128 || F.Py == 256 || F.Py == 512) || yw_smem_bytes<T>(F.Py, 3, 7, 0) > (size_t)smem_max)
+        if (!(F.Py == 64 || F.Py == 128 || F.Py == 256 || F.Py == 512) || yw_smem_bytes<T>(F.Py, 3) > (size_t)smem_max)
             ctx->warp_stray = false;
     if (ctx->warp_stray) {
         std::map<int, std::vector<int4>> ws;
@@ -1262,12 +1262,11 @@ static int setup_t(sgspm_ctx* ctx) {
         }
         for (auto& kv : ws) {
             const int Py = 32 * kv.first;
-            // attributes for the largest staging (every input component read from the cache)
-            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), yw_smem_bytes<T>(Py, 3, 7, 0)};
+            sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), yw_smem_bytes<T>(Py, 3)};
             if ((rc = up4(&c.work, kv.second))) return rc;
-            cudaError_t e1 = attr_yw_n<T, 1>(c.key, yw_smem_bytes<T>(Py, 1, 7, 0));
-            cudaError_t e2 = attr_yw_n<T, 2>(c.key, yw_smem_bytes<T>(Py, 2, 7, 0));
-            cudaError_t e3 = attr_yw_n<T, 3>(c.key, yw_smem_bytes<T>(Py, 3, 7, 0));
+            cudaError_t e1 = attr_yw_n<T, 1>(c.key, yw_smem_bytes<T>(Py, 1));
+            cudaError_t e2 = attr_yw_n<T, 2>(c.key, yw_smem_bytes<T>(Py, 2));
+            cudaError_t e3 = attr_yw_n<T, 3>(c.key, yw_smem_bytes<T>(Py, 3));
             CK(e1);
             CK(e2);
             CK(e3);

@@ -746,16 +746,8 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     const bool zodd = kz > Pz / 2;
     V* stw = reinterpret_cast<V*>(smem_raw);
     V* scr0 = stw + P;
-    V* inb = scr0 + kWarpLines * P;   // per component: [lines][LI] (fresh) or [lines][P] (cached)
-    T* kbuf = reinterpret_cast<T*>(inb + yw_in_elems(P, pg.in_mask, pg.fresh_mask));   // [3 NOUT][lines][HyP]
-    int ioff[3];
-    {
-        int o = 0;
-        for (int b = 0; b < 3; ++b) {
-            ioff[b] = o;
-            if (pg.in_mask & (1 << b)) o += kWarpLines * (((pg.fresh_mask >> b) & 1) ? LI : P);
-        }
-    }
+    V* inb = scr0 + kWarpLines * P;                                       // [3][lines][LI]
+    T* kbuf = reinterpret_cast<T*>(inb + 3 * kWarpLines * LI);            // [3 NOUT][lines][HyP]
     {
         const V* g = d.tw + d.plans[F.plan_py].tw;
         for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = g[i];
@@ -771,18 +763,11 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
         if (pg.in_mask & (1 << b)) {
             const V* Sb = d.spec[pg.in_spec[b]] + line0;
             const bool fresh = (pg.fresh_mask >> b) & 1;
-            V* dst = inb + ioff[b];
+            V* dst = inb + b * kWarpLines * LI;
             const int n = fresh ? tn * ny : 0;
             for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
                 const int y = idx / tn, t = idx - y * tn;
                 cp_async<(int)sizeof(V)>(dst + t * LI + y, Sb + (long long)y * Kx + t);
-            }
-            if (!fresh) {
-                // the tn cached lines (kz, kx0 .. kx0 + tn - 1) are one contiguous block
-                const V* cs = d.ycache + b * d.ycache_n + F.off_ycache + ((long long)kz * Kx + kx0) * P;
-                constexpr int VCH = 16 / (int)sizeof(V);   // complex values per 16-byte piece
-                const int nch = tn * P / VCH;
-                for (int i = threadIdx.x; i < nch; i += blockDim.x) cp_async_16(dst + i * VCH, cs + i * VCH);
             }
 #pragma unroll
             for (int o = 0; o < NOUT; ++o) {
@@ -814,7 +799,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
         V v[E];
         V* cb = d.ycache + b * d.ycache_n + cline;
         if ((pg.fresh_mask >> b) & 1) {
-            const V* line = inb + ioff[b] + warp * LI;
+            const V* line = inb + (b * kWarpLines + warp) * LI;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 const int y = lane + 32 * k;
@@ -826,9 +811,8 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
                 for (int s1 = 0; s1 < E; ++s1) cb[s1 * 32] = v[s1];
             }
         } else {
-            const V* line = inb + ioff[b] + warp * P;   // staged cached transform
 #pragma unroll
-            for (int s1 = 0; s1 < E; ++s1) v[s1] = line[s1 * 32 + lane];
+            for (int s1 = 0; s1 < E; ++s1) v[s1] = cb[s1 * 32];
         }
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) {

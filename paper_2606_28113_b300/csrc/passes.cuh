@@ -83,18 +83,9 @@ constexpr int kWarpLines = 4;   // kx lines (warps) per CTA of the register stra
 
 __host__ __device__ inline int yw_line_stride(int Py) { return Py / 2 + 8; }
 
-// staged input lines of one CTA: a fresh component takes LI complex per line (its y < ny tile),
-// a cached one Py (its y transform in register order); components outside in_mask take none
-__host__ __device__ inline int yw_in_elems(int Py, int in_mask, int fresh_mask) {
-    int n = 0;
-    for (int b = 0; b < 3; ++b)
-        if (in_mask & (1 << b)) n += ((fresh_mask >> b) & 1) ? yw_line_stride(Py) : Py;
-    return kWarpLines * n;
-}
-
 template <typename T>
-__host__ __device__ inline size_t yw_smem_bytes(int Py, int nout, int in_mask = 7, int fresh_mask = 0) {
-    return (size_t)(Py + kWarpLines * Py + yw_in_elems(Py, in_mask, fresh_mask)) * sizeof(cplx<T>) +
+__host__ __device__ inline size_t yw_smem_bytes(int Py, int nout) {
+    return (size_t)(Py + kWarpLines * Py + 3 * kWarpLines * yw_line_stride(Py)) * sizeof(cplx<T>) +
            (size_t)3 * nout * kWarpLines * ktab_row(Py) * sizeof(T);
 }
 
