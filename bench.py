@@ -153,12 +153,14 @@ def run_reference(args):
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands (cold
-# caches; profiles/passes_film256x256x8_fp32.md).  Only valid for the kernel that was captured:
-# set an entry back to None when its kernel changes.
+# caches, full metric set, 256x256x8 film).  Only valid for the kernel that was captured: set an
+# entry back to None when its kernel changes.
 NCU_TRAFFIC = {1: 17.2e6}   # slab pass, right-hand-side launch (kind 1), 256x256x8 FP32
 
 
-# algorithmic bytes per cell of each launch kind, FP32 (field crossings x 4 B; see the design notes)
+# algorithmic bytes per cell of each launch kind, FP32: every operator reads its real operand
+# fields once and writes its real results once (field crossings x 4 B); padded spectra and
+# transposes are implementation overhead, not algorithm
 def algorithmic_bytes_per_cell(kind, ncomp=1):
     k, v = divmod(kind, 10)
     if k == 2:            # stray refresh operator: changed inputs read + outputs written

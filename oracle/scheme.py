@@ -9,7 +9,7 @@ The step follows Sec. 3.2 (SGSPM) and Sec. 3.1 (GSPM) in the paper's order and
 notation, with
     g_i = (I - eps dt Delta_h)^{-1} (m_i + dt f_i),   f = -Q(m2 e2 + m3 e3) + h_s + h_e.
 
-Readings of points the paper leaves open (each is also listed in the design notes):
+Readings of points the paper leaves open:
   * Delta_h: cell-centred 7-point Laplacian with mirror ghosts (oracle/heat.py).
   * When f is evaluated for a g_i^*: at the newest state each time a g is formed
     ("R1", default), so h_s is refreshed at every intermediate state (the remark
