@@ -59,3 +59,15 @@ def test_null_handle_calls_are_rejected():
     assert L.sgspm_sync(None) == sgspm.ERR_ARG
     assert L.sgspm_destroy(None) == sgspm.OK
     assert L.sgspm_create(None, 0.1, 0.1, 0.1, 0.1, None, 0, None, None) == sgspm.ERR_ARG
+
+
+def test_null_handle_tuning_and_parameter_calls_are_rejected():
+    L = sgspm.lib()
+    a = (ctypes.c_double * 1)(0.01)
+    r = (ctypes.c_int * 1)(1)
+    assert L.sgspm_set_alpha(None, a) == sgspm.ERR_ARG
+    assert L.sgspm_xz_classes(None, None, None, 0) == sgspm.ERR_ARG
+    assert L.sgspm_set_packing(None, r, 1) == sgspm.ERR_ARG
+    assert L.sgspm_autotune(None, 1, None, 0) == sgspm.ERR_ARG
+    assert L.sgspm_heat_tile(None) == sgspm.ERR_ARG
+    assert L.sgspm_set_heat_tile(None, 6) == sgspm.ERR_ARG
