@@ -127,32 +127,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         const long long sbase = F.off_spec;
         auto cell_of = [&](int z, int x) -> long long { return cbase + ((long long)z * ny + y) * nx + x; };
         PHASE_MARK(0);
-        // FP32 right-hand-side launches: stage the state row (m1, m2, m3 at y) in shared memory
-        // with cp.async now, so the loads overlap the stray-field inversion below
-        T* sst[3] = {slabs + S, slabs + 2 * S,
-                     reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(smem_raw) + xz_smem_bytes<T>(Lo) -
-                                           xz_smem_stage_bytes<T>(Lo) + 15) & ~(uintptr_t)15)};
-        const bool stg = sizeof(T) == 4 && pg.n_rhs > 0 && pg.rhs_dct && pg.rhs_copy[0] < 0;
-        if (stg) {
-            const bool v16 = (nx % 4 == 0) && ((cbase + (long long)y * nx) % 4 == 0) && (((long long)ny * nx) % 4 == 0);
-            for (int i = 0; i < 3; ++i) {
-                const T* src = d.field[pg.state[i]];
-                if (v16) {
-                    const int nq = nxz / 4;
-                    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                        const int z = (4 * q) / nx, x = 4 * q - z * nx;
-                        cp_async_16(sst[i] + 4 * q, src + cell_of(z, x));
-                    }
-                } else {
-                    for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                        const int z = idx / nx, x = idx - z * nx;
-                        const unsigned s = (unsigned)__cvta_generic_to_shared(sst[i] + idx);
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src + cell_of(z, x)) : "memory");
-                    }
-                }
-            }
-            cp_async_commit();
-        }
         const bool zreg = z_in_registers(nz);
         const T* Cz = sdt;                                       // DCT-II  C[k][n]
         const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
@@ -243,45 +217,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             PHASE_MARK(3);
             if (!pg.rhs_dct) { __syncthreads(); continue; }
             // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
-            if (stg && pg.rhs_copy[ci] < 0) {
-                cp_async_wait(0);
-                __syncthreads();
-                const T* __restrict__ ma = d.field[pg.state[a]];
-                const T* sa = sst[a];
-                const T scale = T(pg.damp ? F.alpha * F.dt : F.dt);
-                const T eps = T(F.eps), Q = T(F.Q);
-                const T ux = T(F.u[0]), uy = T(F.u[1]), uz = T(F.u[2]);
-                const T ua = T(F.u[a]);
-                const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
-                const T hea = T(F.he[a]);
-                constexpr int kB = 4;
-                for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
-                    T yp[kB], ym[kB];
-    #pragma unroll
-                    for (int u = 0; u < kB; ++u) {   // y neighbours (other rows) from global, issued first
-                        const int idx = i0 + u * blockDim.x;
-                        if (idx >= nxz) break;
-                        const int z = idx / nx, x = idx - z * nx;
-                        const long long c = cell_of(z, x);
-                        yp[u] = ma[y + 1 < ny ? c + nx : c];
-                        ym[u] = ma[y > 0 ? c - nx : c];
-                    }
-    #pragma unroll
-                    for (int u = 0; u < kB; ++u) {
-                        const int idx = i0 + u * blockDim.x;
-                        if (idx >= nxz) break;
-                        const int z = idx / nx, x = idx - z * nx;
-                        const T mc = sa[idx];
-                        const T mu = sst[0][idx] * ux + sst[1][idx] * uy + sst[2][idx] * uz;
-                        const T lap = ihx * ((x + 1 < nx ? sa[idx + 1] - mc : T(0)) + (x > 0 ? sa[idx - 1] - mc : T(0))) +
-                                      ihy * ((yp[u] - mc) + (ym[u] - mc)) +
-                                      ihz * ((z + 1 < nz ? sa[idx + nx] - mc : T(0)) + (z > 0 ? sa[idx - nx] - mc : T(0)));
-                        const T he = d.he_cell ? d.he_cell[cell_of(z, x) * 3 + a] : hea;
-                        const T f = -Q * (mc - mu * ua) + h[idx] + he;
-                        h[idx] = scale * (f + eps * lap);
-                    }
-                }
-            } else if (pg.rhs_copy[ci] < 0) {
+            if (pg.rhs_copy[ci] < 0) {
                 const T* __restrict__ m1 = d.field[pg.state[0]];
                 const T* __restrict__ m2 = d.field[pg.state[1]];
                 const T* __restrict__ m3 = d.field[pg.state[2]];

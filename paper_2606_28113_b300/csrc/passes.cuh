@@ -51,17 +51,9 @@ __host__ __device__ inline XZLayout xz_layout(int nx, int nz, int Px, int Pz, in
     return L;
 }
 
-// FP32 form: one more slab (plus 16 bytes of alignment) at the end, where the right-hand-side
-// pass stages the third state component (the other two go to slabs 1 and 2)
-template <typename T>
-__host__ __device__ inline size_t xz_smem_stage_bytes(const XZLayout& L) {
-    return sizeof(T) == 4 ? (size_t)L.slab * sizeof(T) + 16 : 0;
-}
-
 template <typename T>
 __host__ __device__ inline size_t xz_smem_bytes(const XZLayout& L) {
-    return (size_t)(L.tw + 2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)(3 * L.slab + L.dt) * sizeof(T) + (size_t)L.tc +
-           xz_smem_stage_bytes<T>(L);
+    return (size_t)(L.tw + 2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)(3 * L.slab + L.dt) * sizeof(T) + (size_t)L.tc;
 }
 
 // Copy the twiddle tables of `pl` (W_P, and the DCT quarter-wave table when `dct`) from the
