@@ -113,8 +113,8 @@ int sgspm_set_applied_field(sgspm_t h, const double* he);
 
 /*
  * Batch packing of the slab pass (no counterpart in the paper: a launch-shape choice).  Films are
- * grouped in size classes by nx; a class of small slabs (FP32 form, nx <= 128 or not a power of
- * two, not TF32X3) may run several consecutive y rows of a film per CTA.
+ * grouped in size classes by nx; a class (FP32 form, nx <= 256 or not a power of two, not
+ * TF32X3) may run several consecutive y rows of a film per CTA.
  * sgspm_xz_classes: number of classes (>= 0); with keys/rows non-NULL (cap entries) writes each
  *   class's key (nx, or 0 for the runtime-length kernel) and its current rows per CTA.
  * sgspm_set_packing: rows per CTA (1..8), one entry per class; ERR_UNSUPPORTED for > 1 on a

@@ -232,7 +232,7 @@ constexpr int kMaxRowsPerCTA = 8;   // slab pass packing: y rows of one film per
 
 // size classes whose slab pass may pack several y rows per CTA (FP32 form; small slabs)
 static bool packable_class(bool fp64, bool tf32x3, int key) {
-    return !fp64 && !ztc_class(tf32x3, key) && (key == 0 || key == 8 || key == 16 || key == 32 || key == 64 || key == 128);
+    return !fp64 && !ztc_class(tf32x3, key) && key <= 256;
 }
 
 template <typename T>
@@ -246,6 +246,7 @@ static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T
             switch (key) {
                 case 64: launch_pdl(xz_kernel<T, 64, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
                 case 128: launch_pdl(xz_kernel<T, 128, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+                case 256: launch_pdl(xz_kernel<T, 256, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
                 default: launch_pdl(xz_kernel<T, 0, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
             }
         }
@@ -275,6 +276,8 @@ static cudaError_t attr_xz(int key, size_t smem, bool tf32x3) {
                 e = cudaFuncSetAttribute(xz_kernel<T, 64, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             } else if (key == 128) {
                 e = cudaFuncSetAttribute(xz_kernel<T, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            } else if (key == 256) {
+                e = cudaFuncSetAttribute(xz_kernel<T, 256, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             } else {
                 // shared by several classes (runtime x length): allow the most dynamic shared
                 // memory the device gives this kernel (opt-in maximum less its static part)
