@@ -86,14 +86,14 @@ def test_packing_and_autotune_leave_results_unchanged():
 
 def test_tuning_calls_validate_their_arguments():
     f = dict(n=(64, 16, 2), h=(1 / 64,) * 3, eps=0.016, Q=6.2e-4, alpha=0.01, dt=0.01, he=(0.0, 0, 0))
-    g = dict(f, n=(256, 8, 2), h=(1 / 256,) * 3)
+    g = dict(f, n=(512, 8, 2), h=(1 / 512,) * 3)
     H = sgspm.Handle([f, g])
     with pytest.raises(sgspm.SGSPMError) as e:
         H.autotune(2)                          # m not set
     assert e.value.code == sgspm.ERR_STATE
     H.set_m(np.concatenate([inputs.random_unit(1, f["n"]).reshape(-1), inputs.random_unit(2, g["n"]).reshape(-1)]))
     cls = H.xz_classes()
-    assert sorted(k for k, _ in cls) == [64, 256]
+    assert sorted(k for k, _ in cls) == [64, 512]
     with pytest.raises(sgspm.SGSPMError) as e:
         H.set_packing([2] * (len(cls) + 1))    # one entry per class
     assert e.value.code == sgspm.ERR_ARG
@@ -101,7 +101,7 @@ def test_tuning_calls_validate_their_arguments():
         H.set_packing([9] * len(cls))          # rows in 1..8
     assert e.value.code == sgspm.ERR_ARG
     with pytest.raises(sgspm.SGSPMError) as e:
-        H.set_packing([1 if k == 64 else 2 for k, _ in cls])   # the nx 256 class runs one row per CTA
+        H.set_packing([1 if k == 64 else 2 for k, _ in cls])   # the nx 512 class runs one row per CTA
     assert e.value.code == sgspm.ERR_UNSUPPORTED
     with pytest.raises(sgspm.SGSPMError) as e:
         H.set_heat_tile(17)
