@@ -1801,16 +1801,26 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
     void* keep = nullptr;
     CK(cudaMalloc(&keep, 6 * fb + sizeof(long long)));
     char* kp = (char*)keep;
+    // every CUDA error below is recorded and the state restored before returning
+    cudaError_t ce = cudaSuccess;
+    auto ok = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && ce == cudaSuccess) {
+            ce = e;
+            ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+        }
+        return e == cudaSuccess;
+    };
     for (int i = 0; i < 3; ++i) {
-        CK(cudaMemcpyAsync(kp + i * fb, ctx->d_field[M1 + i], fb, cudaMemcpyDeviceToDevice, ctx->stream));
-        if (ctx->d_flo[M1 + i]) CK(cudaMemcpyAsync(kp + (3 + i) * fb, ctx->d_flo[M1 + i], fb, cudaMemcpyDeviceToDevice, ctx->stream));
+        ok(cudaMemcpyAsync(kp + i * fb, ctx->d_field[M1 + i], fb, cudaMemcpyDeviceToDevice, ctx->stream), "autotune: save m");
+        if (ctx->d_flo[M1 + i])
+            ok(cudaMemcpyAsync(kp + (3 + i) * fb, ctx->d_flo[M1 + i], fb, cudaMemcpyDeviceToDevice, ctx->stream), "autotune: save m");
     }
-    CK(cudaMemcpyAsync(kp + 6 * fb, ctx->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, ctx->stream));
+    ok(cudaMemcpyAsync(kp + 6 * fb, ctx->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, ctx->stream), "autotune: save step");
     const long long steps0 = ctx->steps;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    int rc = SGSPM_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ok(cudaEventCreate(&e0), "autotune: event");
+    ok(cudaEventCreate(&e1), "autotune: event");
+    int rc = ce == cudaSuccess ? SGSPM_OK : SGSPM_ERR_CUDA;
     for (int c = 0; c < ncls && !rc; ++c) {
         if (!packable_class(ctx->fp64, ctx->tf32x3, ctx->xz_cls[c].key)) continue;
         int maxny = 1;
@@ -1862,19 +1872,21 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
         }
         if (!rc) rc = ctx->fp64 ? build_heat_classes<double>(ctx, best_tx) : build_heat_classes<float>(ctx, best_tx);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     for (int i = 0; i < 3; ++i) {
-        CK(cudaMemcpyAsync(ctx->d_field[M1 + i], kp + i * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream));
-        if (ctx->d_flo[M1 + i]) CK(cudaMemcpyAsync(ctx->d_flo[M1 + i], kp + (3 + i) * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+        ok(cudaMemcpyAsync(ctx->d_field[M1 + i], kp + i * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream), "autotune: restore m");
+        if (ctx->d_flo[M1 + i])
+            ok(cudaMemcpyAsync(ctx->d_flo[M1 + i], kp + (3 + i) * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream), "autotune: restore m");
     }
-    CK(cudaMemcpyAsync(ctx->d_step, kp + 6 * fb, sizeof(long long), cudaMemcpyDeviceToDevice, ctx->stream));
+    ok(cudaMemcpyAsync(ctx->d_step, kp + 6 * fb, sizeof(long long), cudaMemcpyDeviceToDevice, ctx->stream), "autotune: restore step");
     ctx->steps = steps0;
     int rc2 = run_prog(ctx, ctx->fwd_prog, ctx->stream);   // spectra of the restored state
-    CK(cudaStreamSynchronize(ctx->stream));
+    ok(cudaStreamSynchronize(ctx->stream), "autotune: sync");
     cudaFree(keep);
     if (rc) return rc;
     if (rc2) return rc2;
+    if (ce != cudaSuccess) return ce == cudaErrorMemoryAllocation ? SGSPM_ERR_OOM : SGSPM_ERR_CUDA;
     rc = check_status(ctx);
     if (rc) return rc;
     for (int c = 0; rows_out && c < ncls; ++c) rows_out[c] = ctx->xz_cls[c].rows;
