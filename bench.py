@@ -122,6 +122,18 @@ def cpu_baseline(w, m0, nsteps=4):
                       f"Newell set-up excluded"}, m
 
 
+def whole_job(step_ms, ncell, steps, world, device):
+    """Replicas: every rank advances its own film.  Returns (max over ranks of the timed ms,
+    whole-job cell-steps/s = world x cells x steps / that time)."""
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    return step_ms, world * ncell * steps / (step_ms / 1e3)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -349,12 +361,7 @@ def run_gpu(args):
             H.step(1)
             ev[i][1].record(stream)
         barrier()
-    step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * ncell * args.steps / (step_ms / 1e3)
+    step_ms, value = whole_job(sum(a.elapsed_time(b) for a, b in ev), ncell, args.steps, world, "cuda")
     H.sync()
 
     # ---- dominant kernel: per-launch device times of one step, L2 warm (inside a long run) ---

@@ -1,0 +1,53 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks (replicas only, no collective on
+the data path).  The whole-job value takes the slowest rank's time and counts every rank's cells;
+the reference arm prints from rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, value = bench.whole_job(10.0 * (rank + 1), 1000, 5, world, "cpu")
+    out[rank] = (ms, value, bench.dist_env()[:2])
+    dist.destroy_process_group()
+
+
+def test_whole_job_value_over_two_gloo_ranks():
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        ms, value, env = out[r]
+        assert ms == 20.0                               # the slowest rank's time
+        assert value == pytest.approx(2 * 1000 * 5 / 0.020)
+        assert env == (r, world)
+
+
+def test_reference_arm_prints_on_rank_zero_only(capfd, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        steps, warmup, gpus = 1, 3, 2
+
+    bench.run_reference(A())
+    assert capfd.readouterr().out == ""
