@@ -534,4 +534,50 @@ __device__ __forceinline__ void c2r_put(cplx<T>* ca, int p, int k, int P, cplx<T
     if (k != 0 && 2 * k != P) ca[p * P + (P - k)] = cmk<V>(xa.x + xb.y, xb.x - xa.y);
 }
 
+// ---- zero-padded transforms of length P = 2N as two N-point FFTs ------------------------------
+// Forward, input zero for n >= N:  X[2j] = FFT_N(v)[j],  X[2j+1] = FFT_N(v W_P^n)[j].
+// Inverse, output needed for n < N only:  x[n] = IFFT_N(X_even)[n] + conj(W_P^n) IFFT_N(X_odd)[n].
+// A pair p of real lines (packed as v = a + i b) occupies lines 2p (even k) and 2p+1 (odd k),
+// N values each: spectral index k of pair p sits at half_pos(p, k, N).
+__device__ __forceinline__ int half_pos(int p, int k, int N) { return (2 * p + (k & 1)) * N + (k >> 1); }
+
+template <typename T>
+__device__ __forceinline__ cplx<T> r2c_get_h(const cplx<T>* res, int line, int k, int P) {
+    using V = cplx<T>;
+    const int p = line >> 1, N = P / 2;
+    V Z = res[half_pos(p, k, N)];
+    V Zr = cconj(res[half_pos(p, k == 0 ? 0 : P - k, N)]);
+    return (line & 1) ? cscale(cmul_mi(csub(Z, Zr)), T(0.5)) : cscale(cadd(Z, Zr), T(0.5));
+}
+
+template <typename T>
+__device__ __forceinline__ void c2r_put_h(cplx<T>* ca, int p, int k, int P, cplx<T> xa, cplx<T> xb) {
+    using V = cplx<T>;
+    const int N = P / 2;
+    if (k == 0 || 2 * k == P) { xa.y = T(0); xb.y = T(0); }
+    ca[half_pos(p, k, N)] = cmk<V>(xa.x - xb.y, xa.y + xb.x);
+    if (k != 0 && 2 * k != P) ca[half_pos(p, P - k, N)] = cmk<V>(xa.x + xb.y, xb.x - xa.y);
+}
+
+// Forward zero-padded transform (P = 2N) of L.n real lines of length nlen <= N, as pairs, with
+// N-point FFTs (plan pN); twP = W_P^m (m < P).  Returns the buffer holding the half layout.
+template <typename T, int N>
+__device__ cplx<T>* r2c_lines_h(const T* R, Lines L, int nlen, cplx<T>* ca, cplx<T>* cb, const Plan& pN,
+                                const cplx<T>* __restrict__ twpool, const cplx<T>* __restrict__ twP) {
+    using V = cplx<T>;
+    const int npair = (L.n + 1) / 2;
+    for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
+        const int p = idx / N, n = idx - p * N;
+        V v = cmk<V>(T(0), T(0));
+        if (n < nlen) {
+            v.x = R[(2 * p) * L.ls + n * L.es];
+            if (2 * p + 1 < L.n) v.y = R[(2 * p + 1) * L.ls + n * L.es];
+        }
+        ca[(2 * p) * N + n] = v;
+        ca[(2 * p + 1) * N + n] = cmul(v, twP[n]);
+    }
+    __syncthreads();
+    return fft_lines_t<T, false, N>(ca, cb, Lines{2 * npair, N, 1}, pN, twpool);
+}
+
 }  // namespace sgspm

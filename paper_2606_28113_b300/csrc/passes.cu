@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     const int y0 = wi.y, nrow = MULTI ? (wi.z > 0 ? wi.z : 1) : 1;
     const int nx = F.nx, ny = F.ny, nz = F.nz, Px = F.Px, Pz = F.Pz, Kx = F.Kx;
     const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0, ZTC);
+    // the zero-padded x transform (Px = 2 NX) as two NX-point FFTs per line pair
+    constexpr bool kHalfX = NX >= 64 && NX <= 512;
     __shared__ Plan pdx, pdz, ppx, ppz;
     if (threadIdx.x == 0) {
         // pre-staged plan copies (their twiddle offsets refer to the shared layout below)
@@ -175,7 +177,11 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                         }
     #pragma unroll
                         for (int p = 0; p < kZReg / 2; ++p)
-                            if (2 * p < nz) c2r_put<T>(xw0, p, kx, Px, acc[2 * p], (2 * p + 1 < nz) ? acc[2 * p + 1] : cmk<V>(T(0), T(0)));
+                            if (2 * p < nz) {
+                                const V xb = (2 * p + 1 < nz) ? acc[2 * p + 1] : cmk<V>(T(0), T(0));
+                                if constexpr (kHalfX) c2r_put_h<T>(xw0, p, kx, Px, acc[2 * p], xb);
+                                else c2r_put<T>(xw0, p, kx, Px, acc[2 * p], xb);
+                            }
                     }
                     __syncthreads();
                 }
@@ -191,17 +197,31 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                         int p = idx / kcn, kc = idx - p * kcn;
                         V xa = r[(2 * p) * KC + kc];
                         V xb = (2 * p + 1 < nz) ? r[(2 * p + 1) * KC + kc] : cmk<V>(T(0), T(0));
-                        c2r_put<T>(xw0, p, kc0 + kc, Px, xa, xb);
+                        if constexpr (kHalfX) c2r_put_h<T>(xw0, p, kc0 + kc, Px, xa, xb);
+                        else c2r_put<T>(xw0, p, kc0 + kc, Px, xa, xb);
                     }
                     __syncthreads();
                 }
                 PHASE_MARK(1);
-                V* r = fft_lines_t<T, true, 2 * NX>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
-                PHASE_MARK(2);
-                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                    int z = idx / nx, x = idx - z * nx;
-                    V v = r[(z >> 1) * Px + x];
-                    h[idx] = (z & 1) ? v.y : v.x;
+                if constexpr (kHalfX) {
+                    // two NX-point inverse FFTs per pair; outputs n < nx only
+                    const V* twP = stw + ppx.tw;
+                    V* r = fft_lines_t<T, true, NX>(xw0, xw1, Lines{2 * npx, NX, 1}, pdx, stw);
+                    PHASE_MARK(2);
+                    for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                        int z = idx / nx, x = idx - z * nx;
+                        const int p = z >> 1;
+                        const V v = cadd(r[(2 * p) * NX + x], cmul(r[(2 * p + 1) * NX + x], cconj(twP[x])));
+                        h[idx] = (z & 1) ? v.y : v.x;
+                    }
+                } else {
+                    V* r = fft_lines_t<T, true, 2 * NX>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
+                    PHASE_MARK(2);
+                    for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                        int z = idx / nx, x = idx - z * nx;
+                        V v = r[(z >> 1) * Px + x];
+                        h[idx] = (z & 1) ? v.y : v.x;
+                    }
                 }
             } else {
                 for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) h[idx] = T(0);
@@ -514,7 +534,13 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     src = slabs + (-1 - ref) * S;
                 }
                 PHASE_MARK(11);
-                V* r = r2c_lines<T, 2 * NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
+                V* r;
+                if constexpr (kHalfX) r = r2c_lines_h<T, NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw, stw + ppx.tw);
+                else r = r2c_lines<T, 2 * NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
+                auto rget = [&](int line, int k) {
+                    if constexpr (kHalfX) return r2c_get_h<T>(r, line, k, Px);
+                    else return r2c_get<T>(r, line, k, Px);
+                };
                 PHASE_MARK(12);
                 V* out = d.spec[pg.fwd_dst[i]] + sbase;
                 if (zreg) {
@@ -522,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
                         V v[2 * kZReg];
     #pragma unroll
-                        for (int z = 0; z < 2 * kZReg; ++z) v[z] = z < nz ? r2c_get<T>(r, z, kx, Px) : cmk<V>(T(0), T(0));
+                        for (int z = 0; z < 2 * kZReg; ++z) v[z] = z < nz ? rget(z, kx) : cmk<V>(T(0), T(0));
                         if (zfft_reg<T, false>(v, Pz)) {
     #pragma unroll
                             for (int kz = 0; kz < 2 * kZReg; ++kz)
@@ -547,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     const int kcn = min(KC, Kx - kc0);
                     for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
                         int z = idx / kcn, kc = idx - z * kcn;
-                        zw0[z * KC + kc] = (z < nz) ? r2c_get<T>(r, z, kc0 + kc, Px) : cmk<V>(T(0), T(0));
+                        zw0[z * KC + kc] = (z < nz) ? rget(z, kc0 + kc) : cmk<V>(T(0), T(0));
                     }
                     __syncthreads();
                     V* q = fft_lines<T, false>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
