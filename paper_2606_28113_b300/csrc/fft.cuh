@@ -230,7 +230,8 @@ __device__ __forceinline__ cplx<T>* ct_fft(cplx<T>* a, cplx<T>* b, Lines L, cons
 // the line's scratch region (XOR swizzle, conflict-free); lane (q, g) (G = 32/E lanes per q) takes
 // y_{g + G i}[q], E-point DFT over i, twiddle W_32^{g s1}, then a G-point DIF across the G lanes by
 // shuffles, which leaves X[q + E (s1 + E bitrev(g))] in lane (q, g).  Only __syncwarp inside.
-template <typename T, bool INV, int E>
+// TS: stride into the twiddle table (a table of W_{TS P} serves a P-point FFT with TS > 1)
+template <typename T, bool INV, int E, int TS = 1>
 __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* __restrict__ scr,
                                               const cplx<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
@@ -241,7 +242,7 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
     Bfly<E, INV, V>::run(v);
 #pragma unroll
     for (int q = 1; q < E; ++q) {
-        V w = tw[lane * q];
+        V w = tw[TS * (lane * q)];
         if (INV) w = cconj(w);
         v[q] = cmul(v[q], w);
     }
@@ -255,7 +256,7 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
     if (G > 1) {
 #pragma unroll
         for (int s1 = 1; s1 < E; ++s1) {
-            V w = tw[E * g * s1];
+            V w = tw[TS * (E * g * s1)];
             if (INV) w = cconj(w);
             v[s1] = cmul(v[s1], w);
         }
@@ -263,7 +264,7 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
 #pragma unroll
     for (int d = G / 2; d >= 1; d >>= 1) {
         const bool top = (g & d) == 0;
-        V w = tw[(P / (2 * d)) * (g % d)];
+        V w = tw[TS * ((P / (2 * d)) * (g % d))];
         if (INV) w = cconj(w);
 #pragma unroll
         for (int s1 = 0; s1 < E; ++s1) {
@@ -428,6 +429,9 @@ __device__ __forceinline__ cplx<T>* fft_lines_t(cplx<T>* a, cplx<T>* b, Lines L,
 __device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
 // inverse: sample index stored at position n of v
 __device__ __forceinline__ int mk_src(int n, int N) { return (n < (N + 1) / 2) ? 2 * n : 2 * (N - 1 - n) + 1; }
+// even/odd split of a packed pair p: position k of the pair's length-2N sequence sits at line
+// 2p + (k & 1), index k >> 1, of an [2 pairs][N] layout
+__device__ __forceinline__ int half_pos(int p, int k, int N) { return (2 * p + (k & 1)) * N + (k >> 1); }
 
 // Unnormalised DCT-II  X_k = sum_n x_n cos(pi k (2n+1) / (2N))  of L real lines (in place).
 // R: real lines (R.ls / R.es strides, length N).  ca, cb: complex scratch of >= ceil(L/2) * N.
@@ -436,6 +440,43 @@ __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
                            const cplx<T>* __restrict__ twpool) {
     using V = cplx<T>;
     const int npair = (L.n + 1) / 2;
+    if constexpr (PC >= 128 && PC <= 1024) {
+        // the N-point FFT of each packed pair split by decimation in time into two N/2-point warp
+        // FFTs (even and odd positions), so twice as many warps run half as long
+        constexpr int H = PC / 2;
+        const V* tw = twpool + pl.tw;   // W_N; the half-length FFTs read it with stride 2
+        for (int idx = threadIdx.x; idx < npair * PC; idx += blockDim.x) {
+            int p = idx / PC, j = idx - p * PC;
+            T re = R[(2 * p) * L.ls + j * L.es];
+            T im = (2 * p + 1 < L.n) ? R[(2 * p + 1) * L.ls + j * L.es] : T(0);
+            ca[half_pos(p, mk_pos(j, PC), H)] = cmk<V>(re, im);
+        }
+        __syncthreads();
+        {
+            const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            for (int line = threadIdx.x >> 5; line < 2 * npair; line += nw)
+                warp_fft_line<T, false, H / 32, 2>(ca + line * H, cb + line * H, tw, lane);
+            __syncthreads();
+        }
+        const V* w4 = twpool + pl.tw4;
+        auto zat = [&](int p, int k) {   // Z[k] = E[k'] +- W_N^k' O[k'],  k' = k mod H
+            const int k2 = k < H ? k : k - H;
+            const V e = ca[(2 * p) * H + k2], o = cmul(ca[(2 * p + 1) * H + k2], tw[k2]);
+            return k < H ? cadd(e, o) : csub(e, o);
+        };
+        for (int idx = threadIdx.x; idx < npair * PC; idx += blockDim.x) {
+            int p = idx / PC, k = idx - p * PC;
+            V Z = zat(p, k);
+            V Zr = cconj(zat(p, k == 0 ? 0 : PC - k));
+            V w = w4[k];
+            V va = cscale(cadd(Z, Zr), T(0.5));
+            V vb = cscale(cmul_mi(csub(Z, Zr)), T(0.5));
+            R[(2 * p) * L.ls + k * L.es] = w.x * va.x - w.y * va.y;
+            if (2 * p + 1 < L.n) R[(2 * p + 1) * L.ls + k * L.es] = w.x * vb.x - w.y * vb.y;
+        }
+        __syncthreads();
+        return;
+    }
     Lines C{npair, N, 1};
     for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
         int p = idx / N, j = idx - p * N;
@@ -465,6 +506,46 @@ __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
                            const cplx<T>* __restrict__ twpool) {
     using V = cplx<T>;
     const int npair = (L.n + 1) / 2;
+    if constexpr (PC >= 128 && PC <= 1024) {
+        // inverse N-point FFT split by decimation in frequency into two N/2-point warp FFTs:
+        // z[2m] from C[k] + C[k+H], z[2m+1] from (C[k] - C[k+H]) conj(W_N^k)
+        constexpr int H = PC / 2;
+        const V* tw = twpool + pl.tw;
+        const V* w4 = twpool + pl.tw4;
+        auto cat = [&](int p, int k) {   // the packed pre-twiddled spectrum C[k] of pair p
+            const bool hasb = (2 * p + 1 < L.n);
+            T xa = R[(2 * p) * L.ls + k * L.es];
+            T xar = (k == 0) ? T(0) : R[(2 * p) * L.ls + (PC - k) * L.es];
+            T xb = hasb ? R[(2 * p + 1) * L.ls + k * L.es] : T(0);
+            T xbr = (hasb && k != 0) ? R[(2 * p + 1) * L.ls + (PC - k) * L.es] : T(0);
+            V w = cconj(w4[k]);
+            V va = cmul(w, cmk<V>(xa, -xar));
+            V vb = cmul(w, cmk<V>(xb, -xbr));
+            return cmk<V>(va.x - vb.y, va.y + vb.x);
+        };
+        for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
+            int p = idx / H, k = idx - p * H;
+            const V c0 = cat(p, k), c1 = cat(p, k + H);
+            ca[(2 * p) * H + k] = cadd(c0, c1);
+            ca[(2 * p + 1) * H + k] = cmul(csub(c0, c1), cconj(tw[k]));
+        }
+        __syncthreads();
+        {
+            const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            for (int line = threadIdx.x >> 5; line < 2 * npair; line += nw)
+                warp_fft_line<T, true, H / 32, 2>(ca + line * H, cb + line * H, tw, lane);
+            __syncthreads();
+        }
+        for (int idx = threadIdx.x; idx < npair * PC; idx += blockDim.x) {
+            int p = idx / PC, n = idx - p * PC;
+            V z = ca[(2 * p + (n & 1)) * H + (n >> 1)];
+            int j = mk_src(n, PC);
+            R[(2 * p) * L.ls + j * L.es] = z.x;
+            if (2 * p + 1 < L.n) R[(2 * p + 1) * L.ls + j * L.es] = z.y;
+        }
+        __syncthreads();
+        return;
+    }
     Lines C{npair, N, 1};
     const V* w4 = twpool + pl.tw4;
     for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
@@ -539,7 +620,6 @@ __device__ __forceinline__ void c2r_put(cplx<T>* ca, int p, int k, int P, cplx<T
 // Inverse, output needed for n < N only:  x[n] = IFFT_N(X_even)[n] + conj(W_P^n) IFFT_N(X_odd)[n].
 // A pair p of real lines (packed as v = a + i b) occupies lines 2p (even k) and 2p+1 (odd k),
 // N values each: spectral index k of pair p sits at half_pos(p, k, N).
-__device__ __forceinline__ int half_pos(int p, int k, int N) { return (2 * p + (k & 1)) * N + (k >> 1); }
 
 template <typename T>
 __device__ __forceinline__ cplx<T> r2c_get_h(const cplx<T>* res, int line, int k, int P) {
