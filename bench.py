@@ -167,7 +167,7 @@ def run_reference(args):
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands (cold
 # caches, full metric set, 256x256x8 film).  Only valid for the kernel that was captured: set an
 # entry back to None when its kernel changes.
-NCU_TRAFFIC = {1: None}   # slab pass, right-hand-side launch (kind 1): changed since its capture
+NCU_TRAFFIC = {1: 17.5e6}   # slab pass, right-hand-side launch (kind 1), 256x256x8 FP32
 
 
 # algorithmic bytes per cell of each launch kind, FP32: every operator reads its real operand
