@@ -333,13 +333,13 @@ static cudaError_t attr_yh(int key, size_t smem) {
 // key = E = Py / 32
 template <typename T, int NOUT>
 static void launch_yw_n(int key, int nb, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
-    const unsigned nt = 32 * kWarpLines, nt2 = 64 * kWarpLines;   // one / two warps per line
+    const unsigned nt = 32 * kWarpLines;
     const size_t smem = yw_smem_bytes<T>(32 * key, NOUT);
     switch (key) {
         case 2: launch_pdl(y_stray_warp_kernel<T, NOUT, 2>, nb, nt, smem, st, d, w, pg); break;
-        case 4: launch_pdl(y_stray_split_kernel<T, NOUT, 4>, nb, nt2, smem, st, d, w, pg); break;
-        case 8: launch_pdl(y_stray_split_kernel<T, NOUT, 8>, nb, nt2, smem, st, d, w, pg); break;
-        default: launch_pdl(y_stray_split_kernel<T, NOUT, 16>, nb, nt2, smem, st, d, w, pg); break;
+        case 4: launch_pdl(y_stray_warp_kernel<T, NOUT, 4>, nb, nt, smem, st, d, w, pg); break;
+        case 8: launch_pdl(y_stray_warp_kernel<T, NOUT, 8>, nb, nt, smem, st, d, w, pg); break;
+        default: launch_pdl(y_stray_warp_kernel<T, NOUT, 16>, nb, nt, smem, st, d, w, pg); break;
     }
 }
 template <typename T>
@@ -352,9 +352,9 @@ template <typename T, int NOUT>
 static cudaError_t attr_yw_n(int key, size_t smem) {
     switch (key) {
         case 2: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        case 4: return cudaFuncSetAttribute(y_stray_split_kernel<T, NOUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        case 8: return cudaFuncSetAttribute(y_stray_split_kernel<T, NOUT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        default: return cudaFuncSetAttribute(y_stray_split_kernel<T, NOUT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 4: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 8: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        default: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
 }
 

@@ -281,13 +281,13 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
 
 // Register-resident forward FFT of one line held by a warp: on entry v[k] = x[lane + 32k];
 // on exit v[s1] = X[q + E (s1 + E bitrev_G(g))] with q = lane / G, g = lane % G.
-template <typename T, int E, int TS = 1>
+template <typename T, int E>
 __device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const cplx<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
     Bfly<E, false, V>::run(v);
 #pragma unroll
-    for (int q = 1; q < E; ++q) v[q] = cmul(v[q], tw[TS * (lane * q)]);
+    for (int q = 1; q < E; ++q) v[q] = cmul(v[q], tw[lane * q]);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < E; ++q) scr[q * 32 + (lane ^ ((q * G) & 31))] = v[q];
@@ -298,12 +298,12 @@ __device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ 
     Bfly<E, false, V>::run(v);
     if (G > 1) {
 #pragma unroll
-        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], tw[TS * (E * g * s1)]);
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], tw[E * g * s1]);
     }
 #pragma unroll
     for (int d = G / 2; d >= 1; d >>= 1) {
         const bool top = (g & d) == 0;
-        const V w = tw[TS * ((P / (2 * d)) * (g % d))];
+        const V w = tw[(P / (2 * d)) * (g % d)];
 #pragma unroll
         for (int s1 = 0; s1 < E; ++s1) {
             V pv;
@@ -315,7 +315,7 @@ __device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ 
 }
 
 // The adjoint of wreg_fwd: from the scrambled order back to v[k] = P * IDFT(X)[lane + 32k].
-template <typename T, int E, int TS = 1>
+template <typename T, int E>
 __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const cplx<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
@@ -323,7 +323,7 @@ __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ 
 #pragma unroll
     for (int d = 1; d <= G / 2; d <<= 1) {
         const bool top = (g & d) == 0;
-        const V w = cconj(tw[TS * ((P / (2 * d)) * (g % d))]);
+        const V w = cconj(tw[(P / (2 * d)) * (g % d)]);
 #pragma unroll
         for (int s1 = 0; s1 < E; ++s1) {
             V pv;
@@ -334,7 +334,7 @@ __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ 
     }
     if (G > 1) {
 #pragma unroll
-        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], cconj(tw[TS * (E * g * s1)]));
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], cconj(tw[E * g * s1]));
     }
     Bfly<E, true, V>::run(v);
     __syncwarp();
@@ -344,7 +344,7 @@ __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ 
 #pragma unroll
     for (int qq = 0; qq < E; ++qq) v[qq] = scr[qq * 32 + (lane ^ ((qq * G) & 31))];
 #pragma unroll
-    for (int qq = 1; qq < E; ++qq) v[qq] = cmul(v[qq], cconj(tw[TS * (lane * qq)]));
+    for (int qq = 1; qq < E; ++qq) v[qq] = cmul(v[qq], cconj(tw[lane * qq]));
     Bfly<E, true, V>::run(v);
 }
 

@@ -871,137 +871,6 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     }
 }
 
-// The register stray pass with each line split over two warps (Py = 32 E, E in {4, 8, 16}).  The
-// input of a line is zero for y >= ny = Py/2 and only y < ny of the output is kept, so the Py-point
-// transform splits exactly: warp 2t transforms x (even ky), warp 2t+1 transforms x W_Py^y (odd ky),
-// each with a Py/2-point register FFT; after the Newell multiply each inverts its half and the
-// even warp combines x[y] = IFFT(Y_even)[y] + conj(W_Py^y) IFFT(Y_odd)[y].  Same staging, cache
-// (per half, in register order) and shared-memory layout as y_stray_warp_kernel.
-template <typename T, int NOUT, int E>
-__global__ void __launch_bounds__(64 * kWarpLines) y_stray_split_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
-    using V = cplx<T>;
-    constexpr int P = 32 * E, H = P / 2, E2 = E / 2, G = 32 / E2;
-    constexpr int LI = P / 2 + 8;                 // yw_line_stride
-    constexpr int HyP = ((P / 2 + 1) + 3) & ~3;   // ktab_row
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_launch_dependents();
-    const int4 wi = work[blockIdx.x];
-    const Film& F = d.films[wi.x];
-    const int kz = wi.y, kx0 = wi.z, tn = wi.w;
-    const int ny = F.ny, Kx = F.Kx, Pz = F.Pz, Hz = Pz / 2 + 1;
-    const int kzr = kz <= Pz - kz ? kz : Pz - kz;
-    const bool zodd = kz > Pz / 2;
-    V* stw = reinterpret_cast<V*>(smem_raw);
-    V* scr0 = stw + P;                                                    // [lines][2][H]
-    V* inb = scr0 + kWarpLines * P;                                       // [3][lines][LI]
-    T* kbuf = reinterpret_cast<T*>(inb + 3 * kWarpLines * LI);            // [3 NOUT][lines][HyP]
-    {
-        const V* g = d.tw + d.plans[F.plan_py].tw;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = g[i];
-    }
-    pdl_wait();
-    const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx0;
-    const T* kt = d.ktab + F.off_ktab;
-    constexpr int KCH = 16 / (int)sizeof(T);
-    const int nkch = tn * HyP / KCH;
-#pragma unroll 1
-    for (int b = 0; b < 3; ++b) {
-        if (pg.in_mask & (1 << b)) {
-            const V* Sb = d.spec[pg.in_spec[b]] + line0;
-            V* dst = inb + b * kWarpLines * LI;
-            const int n = ((pg.fresh_mask >> b) & 1) ? tn * ny : 0;
-            for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-                const int y = idx / tn, t = idx - y * tn;
-                cp_async<(int)sizeof(V)>(dst + t * LI + y, Sb + (long long)y * Kx + t);
-            }
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                const int cc = pair_idx(pg.slot[o], b);
-                const T* src = kt + (((long long)cc * Hz + kzr) * Kx + kx0) * HyP;
-                T* kd = kbuf + (o * 3 + b) * kWarpLines * HyP;
-                for (int i = threadIdx.x; i < nkch; i += blockDim.x) cp_async_16(kd + i * KCH, src + i * KCH);
-            }
-        }
-        cp_async_commit();
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = warp >> 1, hb = warp & 1;   // line, half (0: even ky, 1: odd ky)
-    const bool active = t < tn;
-    V* scr = scr0 + warp * H;
-    const int q = lane / G, g = lane % G;
-    const int s2 = bitrev_lanes(g, G);
-    V acc[NOUT][E2];
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-        for (int s1 = 0; s1 < E2; ++s1) acc[o][s1] = cmk<V>(T(0), T(0));
-    const long long cline = F.off_ycache + ((long long)kz * Kx + kx0 + t) * P + hb * H + lane;
-#pragma unroll 1
-    for (int b = 0; b < 3; ++b) {
-        cp_async_wait(2 - b);
-        __syncthreads();
-        if (!active || !(pg.in_mask & (1 << b))) continue;
-        V v[E2];
-        V* cb = d.ycache + b * d.ycache_n + cline;
-        if ((pg.fresh_mask >> b) & 1) {
-            const V* line = inb + (b * kWarpLines + t) * LI;
-#pragma unroll
-            for (int k = 0; k < E2; ++k) {
-                const int y = lane + 32 * k;
-                V x = y < ny ? line[y] : cmk<V>(T(0), T(0));
-                v[k] = hb ? cmul(x, stw[y]) : x;
-            }
-            wreg_fwd<T, E2, 2>(v, scr, stw, lane);
-            if ((pg.store_mask >> b) & 1) {
-#pragma unroll
-                for (int s1 = 0; s1 < E2; ++s1) cb[s1 * 32] = v[s1];
-            }
-        } else {
-#pragma unroll
-            for (int s1 = 0; s1 < E2; ++s1) v[s1] = cb[s1 * 32];
-        }
-#pragma unroll
-        for (int o = 0; o < NOUT; ++o) {
-            const int cc = pair_idx(pg.slot[o], b);
-            const bool yflip = (cc == 3 || cc == 5);
-            const bool zflip = (cc == 4 || cc == 5) && zodd;
-            const T* kb = kbuf + ((o * 3 + b) * kWarpLines + t) * HyP;
-#pragma unroll
-            for (int s1 = 0; s1 < E2; ++s1) {
-                const int ky = 2 * (q + E2 * (s1 + E2 * s2)) + hb;
-                const int kyr = ky <= P / 2 ? ky : P - ky;
-                T k = kb[kyr];
-                if ((yflip && ky > P / 2) != zflip) k = -k;
-                acc[o][s1].x += k * v[s1].x;
-                acc[o][s1].y += k * v[s1].y;
-            }
-        }
-    }
-    const long long out0 = line0 + t;
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o) {
-        if (active) {
-            wreg_adj<T, E2, 2>(acc[o], scr, stw, lane);   // acc[o][k]: half result at y = lane + 32 k
-            if (hb) {
-                __syncwarp();
-#pragma unroll
-                for (int k = 0; k < E2; ++k) scr[lane + 32 * k] = acc[o][k];
-            }
-        }
-        __syncthreads();
-        if (active && !hb) {
-            const V* po = scr0 + (warp + 1) * H;
-            V* Ho = d.spec[pg.out_spec[o]] + out0;
-#pragma unroll
-            for (int k = 0; k < E2; ++k) {
-                const int y = lane + 32 * k;
-                if (y < ny) Ho[(long long)y * Kx] = cadd(acc[o][k], cmul(po[y], cconj(stw[y])));
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // Energy: per-block FP64 partial sums, then an ordered per-film sum (deterministic).
 // work: (film, first cell, count, -)
