@@ -1852,7 +1852,7 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
         for (const Film& F : ctx->films) maxny = std::max(maxny, F.ny);
         float best = 1e30f;
         int best_tx = ctx->tx_h;
-        for (int tx : {4, 6, 8, 12, 16}) {
+        for (int tx : {2, 3, 4, 6, 8, 12, 16}) {
             const size_t sm = ctx->fp64 ? heat_smem<double>(maxny, tx) : heat_smem<float>(maxny, tx);
             if (sm > ctx->smem_max) continue;
             if ((rc = ctx->fp64 ? build_heat_classes<double>(ctx, tx) : build_heat_classes<float>(ctx, tx))) break;
