@@ -568,14 +568,7 @@ static void build_record(sgspm_ctx* ctx) {
     P.push_back(mk_rhs(ctx, {1}, A1, B2, A3, 0));
     P.push_back(mk_yheat({1}, 0));
     P.push_back(mk_gs(ctx, 1, D2SS, B1, M1, slab(0), A3, E3SS, B2, 0));
-    if (st) {
-        if (yc) {
-            P.push_back(ys({0}, 1, 1));
-            P.push_back(ys({1, 2}, 0, 0));
-        } else {
-            P.push_back(ys({0, 1, 2}, 1, 0));
-        }
-    }
+    if (st) P.push_back(ys({0, 1, 2}, 1, 0));
     {
         Launch L = mk_rhs(ctx, {0, 1, 2}, B1, B2, A3, 1);
         if (st)
@@ -837,20 +830,7 @@ static void build_programs(sgspm_ctx* ctx) {
     }
     // Step 2: damping heat flow at m**, Step 3: projection (only the component the last
     // Gauss-Seidel update changed is new: m1 for SGSPM, m3 for GSPM)
-    if (st) {
-        if (!yc) {
-            P.push_back(mk_ystray({0, 1, 2}));
-        } else {
-            // the component the last update changed, transformed and stored; then the other two
-            // outputs from the cache alone (two lighter launches instead of one three-output one)
-            const int fc = gspm ? 2 : 0;
-            std::vector<int> rest;
-            for (int c = 0; c < 3; ++c)
-                if (c != fc) rest.push_back(c);
-            P.push_back(mk_ystray({fc}, 1 << fc, 1 << fc));
-            P.push_back(mk_ystray(rest, 0, 0));
-        }
-    }
+    if (st) P.push_back(R2 ? mk_ystray({0, 1, 2}) : cached({0, 1, 2}, gspm ? 4 : 1, 0));
     P.push_back(mk_rhs(ctx, {0, 1, 2}, m1f, m2f, m3f, 1));
     P.push_back(mk_yheat({0, 1, 2}, 1));
     P.push_back(mk_final(ctx, m1f, m2f, m3f));
