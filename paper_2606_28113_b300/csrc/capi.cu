@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <string>
 #include <vector>
@@ -101,6 +102,7 @@ struct sgspm_ctx {
     int4* d_work_yh = nullptr;
     int n_yh = 0;
     int tx_h = 8;
+    int heat_threads = 256;            // y heat CTA size (128 or 256; the autotuner may change it)
     int4* d_work_ys[4] = {};
     int n_ys[4] = {};
     int tx_s[4] = {};
@@ -308,16 +310,17 @@ static cudaError_t attr_xz(int key, size_t smem, bool tf32x3) {
     }
 }
 template <typename T>
-static void launch_yh(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
+static void launch_yh(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg,
+                      int threads) {
     if constexpr (sizeof(T) == 8) {
-        launch_pdl(y_heat_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg);
+        launch_pdl(y_heat_kernel<T, 0>, nb, (unsigned)threads, smem, st, d, w, pg);
         return;
     }
     switch (key) {
-#define SGSPM_YH(K) case K: launch_pdl(y_heat_kernel<T, K>, nb, kThreads, smem, st, d, w, pg); break;
+#define SGSPM_YH(K) case K: launch_pdl(y_heat_kernel<T, K>, nb, (unsigned)threads, smem, st, d, w, pg); break;
         SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
 #undef SGSPM_YH
-        default: launch_pdl(y_heat_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg);
+        default: launch_pdl(y_heat_kernel<T, 0>, nb, (unsigned)threads, smem, st, d, w, pg);
     }
 }
 template <typename T>
@@ -367,7 +370,7 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
                 launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3, c.rows);
             break;
         case 1:
-            for (const auto& c : ctx->yh_cls) launch_yh<T>(c.key, c.n, c.smem, st, d, c.work, L.y);
+            for (const auto& c : ctx->yh_cls) launch_yh<T>(c.key, c.n, c.smem, st, d, c.work, L.y, ctx->heat_threads);
             break;
         case 2: {
             int n = L.y.n;
@@ -1851,10 +1854,12 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
         int maxny = 1;
         for (const Film& F : ctx->films) maxny = std::max(maxny, F.ny);
         float best = 1e30f;
-        int best_tx = ctx->tx_h;
-        for (int tx : {2, 3, 4, 6, 8, 12, 16}) {
+        int best_tx = ctx->tx_h, best_th = ctx->heat_threads;
+        for (int cand = 0; cand < 14 && !rc; ++cand) {
+            const int tx = std::array<int, 7>{2, 3, 4, 6, 8, 12, 16}[cand % 7], th = cand < 7 ? 256 : 128;
             const size_t sm = ctx->fp64 ? heat_smem<double>(maxny, tx) : heat_smem<float>(maxny, tx);
             if (sm > ctx->smem_max) continue;
+            ctx->heat_threads = th;
             if ((rc = ctx->fp64 ? build_heat_classes<double>(ctx, tx) : build_heat_classes<float>(ctx, tx))) break;
             if ((rc = sgspm_step(ctx, 1))) break;
             if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = SGSPM_ERR_CUDA; break; }
@@ -1868,8 +1873,10 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
             if (ms < best) {
                 best = ms;
                 best_tx = tx;
+                best_th = th;
             }
         }
+        ctx->heat_threads = best_th;
         if (!rc) rc = ctx->fp64 ? build_heat_classes<double>(ctx, best_tx) : build_heat_classes<float>(ctx, best_tx);
     }
     if (e0) cudaEventDestroy(e0);
