@@ -127,7 +127,9 @@ int sgspm_set_applied_field(sgspm_t h, const double* he);
 int sgspm_xz_classes(sgspm_t h, int* keys, int* rows, int cap);
 /* y heat pass: x lines per CTA (1..16; default 8).  sgspm_heat_tile returns the current value;
  * sgspm_set_heat_tile: ERR_ARG outside 1..16, ERR_UNSUPPORTED if the tile does not fit in shared
- * memory.  sgspm_autotune also chooses it (from 2, 3, 4, 6, 8, 12, 16), with a CTA of 128 or 256 threads.  Results do not depend on it. */
+ * memory.  sgspm_autotune also chooses it (from 2, 4, 6, 8, 12, 16), with a CTA of 128 or 256
+ * threads.  Lines are transformed in packed pairs (2i, 2i+1): every even tile gives bitwise the
+ * same results; an odd tile pairs some lines differently (differences at rounding level). */
 int sgspm_heat_tile(sgspm_t h);
 int sgspm_set_heat_tile(sgspm_t h, int tx);
 int sgspm_set_packing(sgspm_t h, const int* rows, int n);

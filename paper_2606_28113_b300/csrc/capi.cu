@@ -1855,8 +1855,10 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
         for (const Film& F : ctx->films) maxny = std::max(maxny, F.ny);
         float best = 1e30f;
         int best_tx = ctx->tx_h, best_th = ctx->heat_threads;
-        for (int cand = 0; cand < 14 && !rc; ++cand) {
-            const int tx = std::array<int, 7>{2, 3, 4, 6, 8, 12, 16}[cand % 7], th = cand < 7 ? 256 : 128;
+        // even tiles only: every tile then pairs x lines (2i, 2i+1) the same way, so the choice
+        // cannot change results
+        for (int cand = 0; cand < 12 && !rc; ++cand) {
+            const int tx = std::array<int, 6>{2, 4, 6, 8, 12, 16}[cand % 6], th = cand < 6 ? 256 : 128;
             const size_t sm = ctx->fp64 ? heat_smem<double>(maxny, tx) : heat_smem<float>(maxny, tx);
             if (sm > ctx->smem_max) continue;
             ctx->heat_threads = th;
