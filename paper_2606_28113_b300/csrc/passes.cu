@@ -78,7 +78,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     // the zero-padded x transform (Px = 2 NX) as two NX-point FFTs per line pair
     constexpr bool kHalfX = NX >= 64 && NX <= 512;
     __shared__ Plan pdx, pdz, ppx, ppz;
-    __shared__ cplx<T> dcbuf[2 * kZReg];   // z spectrum of the packed DC + i Nyquist column
     if (threadIdx.x == 0) {
         // pre-staged plan copies (their twiddle offsets refer to the shared layout below)
         pdx = d.plans[F.splan_dx];
@@ -150,25 +149,15 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             } else if (pg.rhs_h[ci] >= 0 && stray) {
                 const V* H = d.spec[pg.rhs_h[ci]] + sbase;
                 if (zreg) {
-                    // inverse zero-padded DFT along z in registers, one thread per kx column; the
-                    // DC and Nyquist columns (real in x) share one transform as DC + i Nyquist, so
-                    // Kx = nx + 1 columns take nx threads
-                    const int kxn = Kx > 1 ? Kx - 1 : Kx;
-                    for (int kx = threadIdx.x; kx < kxn; kx += blockDim.x) {
-                        const bool dc = kx == 0 && Kx > 1;
+                    // inverse zero-padded DFT along z in registers, one thread per kx column
+                    for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
                         V acc[kZReg];
     #pragma unroll
                         for (int z = 0; z < kZReg; ++z) acc[z] = cmk<V>(T(0), T(0));
                         V hz[2 * kZReg];
     #pragma unroll
-                        for (int kz = 0; kz < 2 * kZReg; ++kz) {
-                            V a = kz < Pz ? H[((long long)kz * ny + y) * Kx + kx] : cmk<V>(T(0), T(0));
-                            if (dc && kz < Pz) {
-                                const V b = H[((long long)kz * ny + y) * Kx + (Kx - 1)];
-                                a = cmk<V>(a.x - b.y, a.y + b.x);
-                            }
-                            hz[kz] = a;
-                        }
+                        for (int kz = 0; kz < 2 * kZReg; ++kz)
+                            hz[kz] = kz < Pz ? H[((long long)kz * ny + y) * Kx + kx] : cmk<V>(T(0), T(0));
                         if (zfft_reg<T, true>(hz, Pz)) {
     #pragma unroll
                             for (int z = 0; z < kZReg; ++z) acc[z] = hz[z];
@@ -189,20 +178,9 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     #pragma unroll
                         for (int p = 0; p < kZReg / 2; ++p)
                             if (2 * p < nz) {
-                                const V xa = acc[2 * p];
                                 const V xb = (2 * p + 1 < nz) ? acc[2 * p + 1] : cmk<V>(T(0), T(0));
-                                if (dc) {   // real part: DC column, imaginary part: Nyquist column
-                                    if constexpr (kHalfX) {
-                                        c2r_put_h<T>(xw0, p, 0, Px, cmk<V>(xa.x, T(0)), cmk<V>(xb.x, T(0)));
-                                        c2r_put_h<T>(xw0, p, Kx - 1, Px, cmk<V>(xa.y, T(0)), cmk<V>(xb.y, T(0)));
-                                    } else {
-                                        c2r_put<T>(xw0, p, 0, Px, cmk<V>(xa.x, T(0)), cmk<V>(xb.x, T(0)));
-                                        c2r_put<T>(xw0, p, Kx - 1, Px, cmk<V>(xa.y, T(0)), cmk<V>(xb.y, T(0)));
-                                    }
-                                } else {
-                                    if constexpr (kHalfX) c2r_put_h<T>(xw0, p, kx, Px, xa, xb);
-                                    else c2r_put<T>(xw0, p, kx, Px, xa, xb);
-                                }
+                                if constexpr (kHalfX) c2r_put_h<T>(xw0, p, kx, Px, acc[2 * p], xb);
+                                else c2r_put<T>(xw0, p, kx, Px, acc[2 * p], xb);
                             }
                     }
                     __syncthreads();
@@ -566,26 +544,15 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 PHASE_MARK(12);
                 V* out = d.spec[pg.fwd_dst[i]] + sbase;
                 if (zreg) {
-                    // zero-padded DFT along z in registers, one thread per kx column; the DC and
-                    // Nyquist columns (real) go through one transform as DC + i Nyquist and are
-                    // separated by Hermitian symmetry
-                    const int kxn = Kx > 1 ? Kx - 1 : Kx;
-                    for (int kx = threadIdx.x; kx < kxn; kx += blockDim.x) {
-                        const bool dc = kx == 0 && Kx > 1;
+                    // zero-padded DFT along z in registers, one thread per kx column
+                    for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
                         V v[2 * kZReg];
     #pragma unroll
-                        for (int z = 0; z < 2 * kZReg; ++z) {
-                            V a = z < nz ? rget(z, kx) : cmk<V>(T(0), T(0));
-                            if (dc && z < nz) a = cmk<V>(a.x, rget(z, Kx - 1).x);
-                            v[z] = a;
-                        }
+                        for (int z = 0; z < 2 * kZReg; ++z) v[z] = z < nz ? rget(z, kx) : cmk<V>(T(0), T(0));
                         if (zfft_reg<T, false>(v, Pz)) {
     #pragma unroll
                             for (int kz = 0; kz < 2 * kZReg; ++kz)
-                                if (kz < Pz) {
-                                    if (dc) dcbuf[kz] = v[kz];
-                                    else out[((long long)kz * ny + y) * Kx + kx] = v[kz];
-                                }
+                                if (kz < Pz) out[((long long)kz * ny + y) * Kx + kx] = v[kz];
                         } else {
                             for (int kz = 0; kz < Pz; ++kz) {
                                 V acc = cmk<V>(T(0), T(0));
@@ -596,15 +563,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                                     m += kz;
                                     if (m >= Pz) m -= Pz;
                                 }
-                                if (dc) dcbuf[kz] = acc;
-                                else out[((long long)kz * ny + y) * Kx + kx] = acc;
-                            }
-                        }
-                        if (dc) {
-                            for (int kz = 0; kz < Pz; ++kz) {
-                                const V C = dcbuf[kz], Cm = cconj(dcbuf[kz == 0 ? 0 : Pz - kz]);
-                                out[((long long)kz * ny + y) * Kx] = cscale(cadd(C, Cm), T(0.5));
-                                out[((long long)kz * ny + y) * Kx + (Kx - 1)] = cscale(cmul_mi(csub(C, Cm)), T(0.5));
+                                out[((long long)kz * ny + y) * Kx + kx] = acc;
                             }
                         }
                     }
