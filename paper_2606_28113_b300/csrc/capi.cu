@@ -11,7 +11,8 @@
 #include "../../include/sgspm.h"
 #include "common.cuh"
 #include "passes.cuh"
-#include "passes.cu"
+#include "launch.cuh"
+#include "misc.cu"
 #include "newell.cu"
 #include "noalloc.cu"
 #include "adjoint.cu"
@@ -208,23 +209,7 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
     return d;
 }
 
-// ---- size-class launchers -------------------------------------------------------------------
-// Pass kernels are launched with programmatic stream serialization (see pdl_wait in the kernels).
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
+// ---- size-class dispatch ---------------------------------------------------------------------
 static int pow2_key(int n, int lo, int hi) { return (n >= lo && n <= hi && (n & (n - 1)) == 0) ? n : 0; }
 
 // size classes whose slab pass runs the tensor-core z transforms in the TF32X3 form
@@ -241,108 +226,107 @@ template <typename T>
 static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray,
                       bool tf32x3, int rows) {
     if constexpr (sizeof(T) == 8) {   // the FP64 form uses the runtime-length kernel only
-        launch_pdl(xz_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg, stray);
+        xz_go<T, 0, false, false>(nb, smem, st, d, w, pg, stray);
         return;
     } else {
         if (rows > 1) {
             switch (key) {
-                case 64: launch_pdl(xz_kernel<T, 64, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
-                case 128: launch_pdl(xz_kernel<T, 128, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
-                case 256: launch_pdl(xz_kernel<T, 256, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
-                default: launch_pdl(xz_kernel<T, 0, false, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+                case 64: xz_go<T, 64, false, true>(nb, smem, st, d, w, pg, stray); return;
+                case 128: xz_go<T, 128, false, true>(nb, smem, st, d, w, pg, stray); return;
+                case 256: xz_go<T, 256, false, true>(nb, smem, st, d, w, pg, stray); return;
+                default: xz_go<T, 0, false, true>(nb, smem, st, d, w, pg, stray); return;
             }
         }
         if (ztc_class(tf32x3, key)) {
             switch (key) {
-                case 128: launch_pdl(xz_kernel<T, 128, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
-                case 256: launch_pdl(xz_kernel<T, 256, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
-                default: launch_pdl(xz_kernel<T, 512, true>, nb, kThreads, smem, st, d, w, pg, stray); return;
+                case 128: xz_go<T, 128, true, false>(nb, smem, st, d, w, pg, stray); return;
+                case 256: xz_go<T, 256, true, false>(nb, smem, st, d, w, pg, stray); return;
+                default: xz_go<T, 512, true, false>(nb, smem, st, d, w, pg, stray); return;
             }
         }
-    }
-    switch (key) {
-#define SGSPM_XZ(K) case K: launch_pdl(xz_kernel<T, K>, nb, kThreads, smem, st, d, w, pg, stray); break;
-        SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
+        switch (key) {
+#define SGSPM_XZ(K) case K: xz_go<T, K, false, false>(nb, smem, st, d, w, pg, stray); break;
+            SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
 #undef SGSPM_XZ
-        default: launch_pdl(xz_kernel<T, 0>, nb, kThreads, smem, st, d, w, pg, stray);
+            default: xz_go<T, 0, false, false>(nb, smem, st, d, w, pg, stray);
+        }
     }
 }
 template <typename T>
 static cudaError_t attr_xz(int key, size_t smem, bool tf32x3) {
     if constexpr (sizeof(T) == 8) {
-        return cudaFuncSetAttribute(xz_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return xz_attr<T, 0, false, false>(smem);
     } else {
         if (packable_class(false, tf32x3, key)) {
             cudaError_t e;
             if (key == 64) {
-                e = cudaFuncSetAttribute(xz_kernel<T, 64, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = xz_attr<T, 64, false, true>(smem);
             } else if (key == 128) {
-                e = cudaFuncSetAttribute(xz_kernel<T, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = xz_attr<T, 128, false, true>(smem);
             } else if (key == 256) {
-                e = cudaFuncSetAttribute(xz_kernel<T, 256, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = xz_attr<T, 256, false, true>(smem);
             } else {
                 // shared by several classes (runtime x length): allow the most dynamic shared
                 // memory the device gives this kernel (opt-in maximum less its static part)
                 int dev = 0, mx = 0;
                 cudaGetDevice(&dev);
                 cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-                cudaFuncAttributes fa;
-                e = cudaFuncGetAttributes(&fa, xz_kernel<T, 0, false, true>);
-                if (e != cudaSuccess) return e;
-                e = cudaFuncSetAttribute(xz_kernel<T, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         std::max(mx - (int)fa.sharedSizeBytes, (int)smem));
+                const long long st = xz_static_smem<T, 0, false, true>();
+                if (st < 0) return (cudaError_t)(-st);
+                e = xz_attr<T, 0, false, true>(std::max(mx - (int)st, (int)smem));
             }
             if (e != cudaSuccess) return e;
         }
         if (ztc_class(tf32x3, key)) {
             switch (key) {
-                case 128: return cudaFuncSetAttribute(xz_kernel<T, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                case 256: return cudaFuncSetAttribute(xz_kernel<T, 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                default: return cudaFuncSetAttribute(xz_kernel<T, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                case 128: return xz_attr<T, 128, true, false>(smem);
+                case 256: return xz_attr<T, 256, true, false>(smem);
+                default: return xz_attr<T, 512, true, false>(smem);
             }
         }
-    }
-    switch (key) {
-#define SGSPM_XZ(K) case K: return cudaFuncSetAttribute(xz_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
+        switch (key) {
+#define SGSPM_XZ(K) case K: return xz_attr<T, K, false, false>(smem);
+            SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
 #undef SGSPM_XZ
-        default: return cudaFuncSetAttribute(xz_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            default: return xz_attr<T, 0, false, false>(smem);
+        }
     }
 }
 template <typename T>
 static void launch_yh(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg,
                       int threads) {
     if constexpr (sizeof(T) == 8) {
-        launch_pdl(y_heat_kernel<T, 0>, nb, (unsigned)threads, smem, st, d, w, pg);
-        return;
-    }
-    switch (key) {
-#define SGSPM_YH(K) case K: launch_pdl(y_heat_kernel<T, K>, nb, (unsigned)threads, smem, st, d, w, pg); break;
-        SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
+        yh_go<T, 0>(nb, (unsigned)threads, smem, st, d, w, pg);
+    } else {
+        switch (key) {
+#define SGSPM_YH(K) case K: yh_go<T, K>(nb, (unsigned)threads, smem, st, d, w, pg); break;
+            SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
 #undef SGSPM_YH
-        default: launch_pdl(y_heat_kernel<T, 0>, nb, (unsigned)threads, smem, st, d, w, pg);
+            default: yh_go<T, 0>(nb, (unsigned)threads, smem, st, d, w, pg);
+        }
     }
 }
 template <typename T>
 static cudaError_t attr_yh(int key, size_t smem) {
-    if constexpr (sizeof(T) == 8) return cudaFuncSetAttribute(y_heat_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    switch (key) {
-#define SGSPM_YH(K) case K: return cudaFuncSetAttribute(y_heat_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
+    if constexpr (sizeof(T) == 8) {
+        return yh_attr<T, 0>(smem);
+    } else {
+        switch (key) {
+#define SGSPM_YH(K) case K: return yh_attr<T, K>(smem);
+            SGSPM_YH(8) SGSPM_YH(16) SGSPM_YH(32) SGSPM_YH(64) SGSPM_YH(128) SGSPM_YH(256) SGSPM_YH(512)
 #undef SGSPM_YH
-        default: return cudaFuncSetAttribute(y_heat_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            default: return yh_attr<T, 0>(smem);
+        }
     }
 }
 // key = E = Py / 32
 template <typename T, int NOUT>
 static void launch_yw_n(int key, int nb, cudaStream_t st, const Dev<T>& d, const int4* w, const YProg& pg) {
-    const unsigned nt = 32 * kWarpLines;
-    const size_t smem = yw_smem_bytes<T>(32 * key, NOUT);
     switch (key) {
-        case 2: launch_pdl(y_stray_warp_kernel<T, NOUT, 2>, nb, nt, smem, st, d, w, pg); break;
-        case 4: launch_pdl(y_stray_warp_kernel<T, NOUT, 4>, nb, nt, smem, st, d, w, pg); break;
-        case 8: launch_pdl(y_stray_warp_kernel<T, NOUT, 8>, nb, nt, smem, st, d, w, pg); break;
-        default: launch_pdl(y_stray_warp_kernel<T, NOUT, 16>, nb, nt, smem, st, d, w, pg); break;
+        case 2: yw_go<T, NOUT, 2>(nb, st, d, w, pg); break;
+        case 4: yw_go<T, NOUT, 4>(nb, st, d, w, pg); break;
+        case 8: yw_go<T, NOUT, 8>(nb, st, d, w, pg); break;
+        default: yw_go<T, NOUT, 16>(nb, st, d, w, pg); break;
     }
 }
 template <typename T>
@@ -354,10 +338,10 @@ static void launch_yw(int key, int nout, int nb, cudaStream_t st, const Dev<T>& 
 template <typename T, int NOUT>
 static cudaError_t attr_yw_n(int key, size_t smem) {
     switch (key) {
-        case 2: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        case 4: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        case 8: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        default: return cudaFuncSetAttribute(y_stray_warp_kernel<T, NOUT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 2: return yw_attr<T, NOUT, 2>(smem);
+        case 4: return yw_attr<T, NOUT, 4>(smem);
+        case 8: return yw_attr<T, NOUT, 8>(smem);
+        default: return yw_attr<T, NOUT, 16>(smem);
     }
 }
 
@@ -377,7 +361,7 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
             if (ctx->warp_stray) {
                 for (const auto& c : ctx->yw_cls) launch_yw<T>(c.key, n, c.n, st, d, c.work, L.y);
             } else {
-                y_stray_kernel<T><<<ctx->n_ys[n], kThreads, ctx->smem_ys[n], st>>>(d, ctx->d_work_ys[n], L.y, ctx->tx_s[n]);
+                ys_go<T>(ctx->n_ys[n], ctx->smem_ys[n], st, d, ctx->d_work_ys[n], L.y, ctx->tx_s[n]);
             }
             break;
         }
@@ -1208,8 +1192,7 @@ static int setup_t(sgspm_ctx* ctx) {
         if (ctx->smem_ys[n] > (size_t)smem_max)
             return fail(ctx, SGSPM_ERR_UNSUPPORTED, "y line of length " + std::to_string(maxPy) + " does not fit in shared memory");
     }
-    CK(cudaFuncSetAttribute(y_stray_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)std::max(ctx->smem_ys[1], std::max(ctx->smem_ys[2], ctx->smem_ys[3]))));
+    CK(ys_attr<T>(std::max(ctx->smem_ys[1], std::max(ctx->smem_ys[2], ctx->smem_ys[3]))));
     // work lists: slab and heat passes per size class (films of one x / y length share a launch)
     std::vector<int4> we;
     std::vector<int> first_e;
@@ -2055,18 +2038,6 @@ int sgspm_grad(sgspm_t ctx, const void* dL_dmT, int dtype, void* dL_dhe, double*
                      : grad_t<float>(ctx, dL_dmT, dtype, dL_dhe, dL_dalpha);
 }
 
-#ifdef SGSPM_PHASE_TIMING
-// instrumented builds only: clock64 stamps of block 0 of the last slab pass
-int sgspm_debug_phase_clk(long long* out) {
-    cudaDeviceSynchronize();
-    return cudaMemcpyFromSymbol(out, g_phase_clk, 64 * sizeof(long long)) == cudaSuccess ? 0 : -3;
-}
-int sgspm_debug_run_launch(sgspm_t ctx, int i) {
-    int rc = enqueue(ctx, ctx->step_prog[i], ctx->stream);
-    cudaStreamSynchronize(ctx->stream);
-    return rc ? rc : ctx->step_prog[i].kind * 10 + (ctx->step_prog[i].kind == 0 ? (ctx->step_prog[i].xz.n_rhs ? 1 : ctx->step_prog[i].xz.op == 2 ? 3 : 2) : ctx->step_prog[i].y.n);
-}
-#endif
 
 int sgspm_launches_per_step(sgspm_t ctx) {
     if (!ctx) return SGSPM_ERR_ARG;

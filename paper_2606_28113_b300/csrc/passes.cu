@@ -1,5 +1,5 @@
-// XZ slab pass, Y line pass, energy reduction and small helper kernels (FP32 and FP64).
-// Compiled as part of capi.cu (single translation unit).
+// XZ slab pass and Y line passes (FP32 and FP64).  Included by the kernel translation units
+// (k_*.cu), which instantiate each size class once.
 #pragma once
 #include "passes.cuh"
 
@@ -50,13 +50,6 @@ __device__ __forceinline__ bool zfft_reg(cplx<T> (&v)[2 * kZReg], int P) {
     }
 }
 
-#ifdef SGSPM_PHASE_TIMING
-__device__ long long g_phase_clk[64];
-#define PHASE_MARK(k) do { if (blockIdx.x == 0 && threadIdx.x == 0) g_phase_clk[k] = clock64(); } while (0)
-#else
-#define PHASE_MARK(k) do { } while (0)
-#endif
-
 // ------------------------------------------------------------------------------------------
 // XZ slab pass
 // ------------------------------------------------------------------------------------------
@@ -68,7 +61,6 @@ template <typename T, int NX, bool ZTC = false, bool MULTI = false>
 __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PHASE_MARK(14);
     pdl_launch_dependents();
     const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
@@ -128,7 +120,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         const long long cbase = F.off_cell;
         const long long sbase = F.off_spec;
         auto cell_of = [&](int z, int x) -> long long { return cbase + ((long long)z * ny + y) * nx + x; };
-        PHASE_MARK(0);
         const bool zreg = z_in_registers(nz);
         const T* Cz = sdt;                                       // DCT-II  C[k][n]
         const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
@@ -202,12 +193,10 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     }
                     __syncthreads();
                 }
-                PHASE_MARK(1);
                 if constexpr (kHalfX) {
                     // two NX-point inverse FFTs per pair; outputs n < nx only
                     const V* twP = stw + ppx.tw;
                     V* r = fft_lines_t<T, true, NX>(xw0, xw1, Lines{2 * npx, NX, 1}, pdx, stw);
-                    PHASE_MARK(2);
                     for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
                         int z = idx / nx, x = idx - z * nx;
                         const int p = z >> 1;
@@ -216,7 +205,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     }
                 } else {
                     V* r = fft_lines_t<T, true, 2 * NX>(xw0, xw1, Lines{npx, Px, 1}, ppx, stw);
-                    PHASE_MARK(2);
                     for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
                         int z = idx / nx, x = idx - z * nx;
                         V v = r[(z >> 1) * Px + x];
@@ -234,7 +222,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     out[cell_of(z, x)] = h[idx];
                 }
             }
-            PHASE_MARK(3);
             if (!pg.rhs_dct) { __syncthreads(); continue; }
             // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
             if (pg.rhs_copy[ci] < 0) {
@@ -288,9 +275,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 }
             }
             __syncthreads();
-            PHASE_MARK(4);
             dct2_lines<T, NX>(h, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
-            PHASE_MARK(5);
             bool zdone = false;
             if constexpr (ZTC) {
                 if (tcz) {
@@ -328,7 +313,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             __syncthreads();
         }
 
-        PHASE_MARK(6);
         // ---- phase I: inverse DCT of solved spectra -> delta slabs ------------------------------
         for (int i = 0; i < pg.n_inv; ++i) {
             T* s = slabs + i * S;
@@ -366,9 +350,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             } else {
                 dct3_lines<T>(s, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
             }
-            PHASE_MARK(7);
             dct3_lines<T, NX>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
-            PHASE_MARK(8);
             if (pg.inv_store[i] >= 0) {
                 T* out = d.field[pg.inv_store[i]];
                 for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
@@ -378,7 +360,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             }
         }
 
-        PHASE_MARK(9);
         // ---- phase U: pointwise updates ----------------------------------------------------------
         if (pg.op == 1) {
             // Gauss-Seidel cross product: out = base + p*q - r*s  (delta form, see host program)
@@ -515,7 +496,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             __syncthreads();
         }
 
-        PHASE_MARK(10);
         // ---- phase F: forward zero-padded FFT (x R2C, z C2C) -> spectral slots ---------------------
         if (stray) {
             for (int i = 0; i < pg.n_fwd; ++i) {
@@ -533,7 +513,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 } else {
                     src = slabs + (-1 - ref) * S;
                 }
-                PHASE_MARK(11);
                 V* r;
                 if constexpr (kHalfX) r = r2c_lines_h<T, NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw, stw + ppx.tw);
                 else r = r2c_lines<T, 2 * NX>(src, Lines{nz, nx, 1}, nx, xw0, xw1, ppx, stw);
@@ -541,7 +520,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     if constexpr (kHalfX) return r2c_get_h<T>(r, line, k, Px);
                     else return r2c_get<T>(r, line, k, Px);
                 };
-                PHASE_MARK(12);
                 V* out = d.spec[pg.fwd_dst[i]] + sbase;
                 if (zreg) {
                     // zero-padded DFT along z in registers, one thread per kx column
@@ -585,7 +563,6 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 }
             }
         }
-        PHASE_MARK(13);
         if constexpr (MULTI) __syncthreads();   // the next row reuses every shared buffer
     }
     if constexpr (ZTC) {
@@ -870,152 +847,5 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
         }
     }
 }
-
-// ------------------------------------------------------------------------------------------
-// Energy: per-block FP64 partial sums, then an ordered per-film sum (deterministic).
-// work: (film, first cell, count, -)
-// ------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) energy_partial_kernel(Dev<T> d, const int4* __restrict__ work, int m0, int hs0,
-                                                                  int have_hs, double* __restrict__ part) {
-    const int4 wi = work[blockIdx.x];
-    const Film F = d.films[wi.x];
-    const int nx = F.nx, ny = F.ny, nz = F.nz;
-    const long long sxy = (long long)nx * ny;
-    const T* m[3] = {d.field[m0], d.field[m0 + 1], d.field[m0 + 2]};
-    double ex = 0, an = 0, st = 0, ze = 0;
-    for (int i = threadIdx.x; i < wi.z; i += blockDim.x) {
-        long long loc = wi.y + i;
-        int x = loc % nx;
-        int y = (loc / nx) % ny;
-        int z = loc / sxy;
-        long long c = F.off_cell + loc;
-        const T* ml[3] = {d.flo[m0], d.flo[m0 + 1], d.flo[m0 + 2]};
-        auto val = [&](int a, long long cc) -> double { return (double)m[a][cc] + (ml[a] ? (double)ml[a][cc] : 0.0); };
-        double v[3] = {val(0, c), val(1, c), val(2, c)};
-        for (int a = 0; a < 3; ++a) {
-            if (x + 1 < nx) { double q = val(a, c + 1) - v[a]; ex += q * q / (F.hx * F.hx); }
-            if (y + 1 < ny) { double q = val(a, c + nx) - v[a]; ex += q * q / (F.hy * F.hy); }
-            if (z + 1 < nz) { double q = val(a, c + sxy) - v[a]; ex += q * q / (F.hz * F.hz); }
-        }
-        double mu = v[0] * F.u[0] + v[1] * F.u[1] + v[2] * F.u[2];
-        an += v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - mu * mu;
-        if (have_hs)
-            for (int a = 0; a < 3; ++a) st += (double)d.field[hs0 + a][c] * v[a];
-        for (int a = 0; a < 3; ++a) {
-            double he = d.he_cell ? (double)d.he_cell[c * 3 + a] : F.he[a];
-            ze += he * v[a];
-        }
-    }
-    __shared__ double red[4][kThreads / 32];
-    double vals[4] = {ex, an, st, ze};
-    for (int k = 0; k < 4; ++k) {
-        double s = vals[k];
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        double s = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
-        part[blockIdx.x * 4 + threadIdx.x] = s;
-    }
-}
-
-// one thread per film: sum the film's block partials in order and apply the prefactors
-__global__ void energy_final_kernel(const Film* films, int nfilm, const int* __restrict__ first_block,
-                                    const double* __restrict__ part, double* __restrict__ out) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfilm) return;
-    const Film F = films[f];
-    double s[4] = {0, 0, 0, 0};
-    for (int b = first_block[f]; b < first_block[f + 1]; ++b)
-        for (int k = 0; k < 4; ++k) s[k] += part[b * 4 + k];
-    const double V = F.hx * F.hy * F.hz;
-    double ex = 0.5 * F.eps * V * s[0];
-    double an = 0.5 * F.Q * V * s[1];
-    double st = -0.5 * V * s[2];
-    double ze = -V * s[3];
-    out[5 * f + 0] = ex;
-    out[5 * f + 1] = an;
-    out[5 * f + 2] = st;
-    out[5 * f + 3] = ze;
-    out[5 * f + 4] = ex + an + st + ze;
-}
-
-// ------------------------------------------------------------------------------------------
-// helpers: dtype conversion in/out of the SoA pools, normalisation, step counter
-// ------------------------------------------------------------------------------------------
-template <typename T, typename S>
-__global__ void copy_in_kernel(T* __restrict__ d0, T* __restrict__ d1, T* __restrict__ d2, T* __restrict__ l0,
-                               T* __restrict__ l1, T* __restrict__ l2, const S* __restrict__ src,
-                               const Film* films, int nfilm, long long ntot) {
-    // src: concatenation over films of [3][ncell_f]
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= ntot) return;
-    int f = 0;
-    while (f + 1 < nfilm && films[f + 1].off_cell <= i) ++f;
-    const Film F = films[f];
-    long long loc = i - F.off_cell;
-    long long nc = (long long)F.nx * F.ny * F.nz;
-    const S* s = src + 3 * F.off_cell;
-    T* dd[3] = {d0, d1, d2};
-    T* ll[3] = {l0, l1, l2};
-    for (int a = 0; a < 3; ++a) {
-        const double v = (double)s[a * nc + loc];
-        dd[a][i] = (T)v;
-        if (ll[a]) ll[a][i] = (T)(v - (double)(T)v);
-    }
-}
-
-template <typename T, typename S>
-__global__ void copy_out_kernel(S* __restrict__ dst, const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
-                                const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2,
-                                const Film* films, int nfilm, long long ntot) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= ntot) return;
-    int f = 0;
-    while (f + 1 < nfilm && films[f + 1].off_cell <= i) ++f;
-    const Film F = films[f];
-    long long loc = i - F.off_cell;
-    long long nc = (long long)F.nx * F.ny * F.nz;
-    S* s = dst + 3 * F.off_cell;
-    const T* dd[3] = {d0, d1, d2};
-    const T* ll[3] = {l0, l1, l2};
-    for (int a = 0; a < 3; ++a) s[a * nc + loc] = (S)((double)dd[a][i] + (ll[a] ? (double)ll[a][i] : 0.0));
-}
-
-template <typename T>
-__global__ void normalize_kernel(T* m0, T* m1, T* m2, T* l0, T* l1, T* l2, long long n, int* status) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T* mm[3] = {m0, m1, m2};
-    T* ll[3] = {l0, l1, l2};
-    double v[3];
-    for (int a = 0; a < 3; ++a) v[a] = (double)mm[a][i] + (ll[a] ? (double)ll[a][i] : 0.0);
-    double n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    if (!(n2 > 0.0) || !isfinite(n2)) {
-        atomicOr(status, 2);
-        return;
-    }
-    double inv = 1.0 / sqrt(n2);
-    for (int a = 0; a < 3; ++a) {
-        double w = v[a] * inv;
-        mm[a][i] = (T)w;
-        if (ll[a]) ll[a][i] = (T)(w - (double)(T)w);
-    }
-}
-
-template <typename T>
-__global__ void he_interleave_kernel(T* __restrict__ dst, const T* __restrict__ a, const T* __restrict__ b,
-                                     const T* __restrict__ c, long long n) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    dst[3 * i] = a[i];
-    dst[3 * i + 1] = b[i];
-    dst[3 * i + 2] = c[i];
-}
-
-__global__ void step_counter_kernel(long long* ctr) { *ctr += 1; }
 
 }  // namespace sgspm
