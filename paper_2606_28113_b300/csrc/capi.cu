@@ -64,6 +64,7 @@ struct sgspm_ctx {
     Plan* d_plans = nullptr;
     void* d_tw = nullptr;
     void* d_lam = nullptr;
+    void* d_lam_lo = nullptr;          // low parts of the eigenvalues (FP32 form)
     void* d_dtab = nullptr;
     void* d_ktab = nullptr;
     void* d_field[kMaxSlots] = {};
@@ -194,8 +195,9 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
     Dev<T> d;
     d.films = ctx->d_films;
     d.plans = ctx->d_plans;
-    d.tw = (const cplx<T>*)ctx->d_tw;
+    d.tw = (const tw_t<T>*)ctx->d_tw;
     d.lam = (const T*)ctx->d_lam;
+    d.lam_lo = (const T*)ctx->d_lam_lo;
     d.dtab = (const T*)ctx->d_dtab;
     d.ktab = (const T*)ctx->d_ktab;
     d.field = (T* const*)ctx->d_tab;
@@ -950,13 +952,10 @@ static int get_plan(sgspm_ctx* ctx, int P, std::vector<double2>& tw) {
 
 template <typename T>
 static int upload_tw(sgspm_ctx* ctx, const std::vector<double2>& tw) {
-    std::vector<cplx<T>> v(tw.size());
-    for (size_t i = 0; i < tw.size(); ++i) {
-        v[i].x = (T)tw[i].x;
-        v[i].y = (T)tw[i].y;
-    }
-    CK(cudaMalloc(&ctx->d_tw, v.size() * sizeof(cplx<T>)));
-    CK(cudaMemcpy(ctx->d_tw, v.data(), v.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+    std::vector<tw_t<T>> v(tw.size());
+    for (size_t i = 0; i < tw.size(); ++i) v[i] = tw_make(tw[i].x, tw[i].y, (T*)nullptr);
+    CK(cudaMalloc(&ctx->d_tw, v.size() * sizeof(tw_t<T>)));
+    CK(cudaMemcpy(ctx->d_tw, v.data(), v.size() * sizeof(tw_t<T>), cudaMemcpyHostToDevice));
     return SGSPM_OK;
 }
 
@@ -1043,7 +1042,7 @@ static int newell_setup(sgspm_ctx* ctx, const Film& F) {
 template <typename T>
 static size_t heat_smem(int ny, int tx) {
     const size_t V = sizeof(cplx<T>);
-    return (size_t)2 * ny * V + (size_t)2 * ((tx + 1) / 2) * ny * V + (size_t)tx * (ny + 8) * sizeof(T);
+    return (size_t)2 * ny * sizeof(tw_t<T>) + (size_t)2 * ((tx + 1) / 2) * ny * V + (size_t)tx * (ny + 8) * sizeof(T);
 }
 
 // (Re)build the y heat pass's size classes with tx x lines per CTA (a tuning knob).
@@ -1177,7 +1176,7 @@ static int setup_t(sgspm_ctx* ctx) {
         if (F.ny > maxny) maxny = F.ny;
     }
     ctx->tx_h = 8;
-    sy = (size_t)2 * maxny * V + (size_t)2 * ((ctx->tx_h + 1) / 2) * maxny * V + (size_t)ctx->tx_h * (maxny + 8) * sizeof(T);
+    sy = heat_smem<T>(maxny, ctx->tx_h);
     if (sx > (size_t)smem_max || sy > (size_t)smem_max)
         return fail(ctx, SGSPM_ERR_UNSUPPORTED, "slab of " + std::to_string(sx) + " B does not fit in shared memory");
     ctx->smem_xz = sx;
@@ -1188,7 +1187,7 @@ static int setup_t(sgspm_ctx* ctx) {
         if (tx > 16) tx = 16;
         if (tx < 1) tx = 1;
         ctx->tx_s[n] = tx;
-        ctx->smem_ys[n] = (size_t)maxPy * V + (size_t)(2 + n) * tx * (maxPy + 4) * V;
+        ctx->smem_ys[n] = (size_t)maxPy * sizeof(tw_t<T>) + (size_t)(2 + n) * tx * (maxPy + 4) * V;
         if (ctx->smem_ys[n] > (size_t)smem_max)
             return fail(ctx, SGSPM_ERR_UNSUPPORTED, "y line of length " + std::to_string(maxPy) + " does not fit in shared memory");
     }
@@ -1269,6 +1268,11 @@ static int setup_t(sgspm_ctx* ctx) {
     // tables
     if ((rc = upload_tw<T>(ctx, tw))) return rc;
     if ((rc = upload_vec<T>(ctx, &ctx->d_lam, lam))) return rc;
+    if (sizeof(T) == 4) {
+        std::vector<double> lo(lam.size());
+        for (size_t i = 0; i < lam.size(); ++i) lo[i] = lam[i] - (double)(T)lam[i];
+        if ((rc = upload_vec<T>(ctx, &ctx->d_lam_lo, lo))) return rc;
+    }
     if (ctx->dtab_host.empty()) ctx->dtab_host.push_back(0.0);
     if ((rc = upload_vec<T>(ctx, &ctx->d_dtab, ctx->dtab_host))) return rc;
     CK(cudaMalloc(&ctx->d_films, ctx->films.size() * sizeof(Film)));
@@ -1317,7 +1321,7 @@ static int setup_t(sgspm_ctx* ctx) {
 
 static void release(sgspm_ctx* ctx) {
     drop_graph(ctx);
-    void* ptrs[] = {ctx->d_films, ctx->d_plans, ctx->d_tw, ctx->d_lam, ctx->d_dtab, ctx->d_ktab, ctx->d_he, ctx->d_status, ctx->d_step,
+    void* ptrs[] = {ctx->d_films, ctx->d_plans, ctx->d_tw, ctx->d_lam, ctx->d_lam_lo, ctx->d_dtab, ctx->d_ktab, ctx->d_he, ctx->d_status, ctx->d_step,
                     ctx->d_stage, ctx->d_work_xz, ctx->d_work_yh, ctx->d_work_e, ctx->d_first_e, ctx->d_epart, ctx->d_eout,
                     ctx->d_work_yw};
     for (void* p : ptrs)

@@ -21,6 +21,57 @@ template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s)
 template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return cmk<V>(a.y, -a.x); }
 template <typename V> __device__ __forceinline__ V cmul_pi(V a) { return cmk<V>(-a.y, a.x); }
 
+// ---- twiddle factors ---------------------------------------------------------------------------
+// A twiddle table entry.  FP64: the complex value.  FP32: the value split into hi = fl(w) and
+// lo = fl(w - hi) (x, y = hi; z, w = lo), so that a multiplication by a table entry carries the
+// table's own rounding (a fixed relative error of ~3e-8 per entry, identical in every time step,
+// which would otherwise act like a perturbed operator and add up coherently over many steps)
+// down to ~1e-15; only the rounding of the products themselves remains.
+template <typename T> struct TwOf;
+template <> struct TwOf<float> { using type = float4; };
+template <> struct TwOf<double> { using type = double2; };
+template <typename T> using tw_t = typename TwOf<T>::type;
+
+__host__ __device__ __forceinline__ float4 tw_make(double re, double im, float*) {
+    const float hr = (float)re, hi = (float)im;
+    return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+}
+__host__ __device__ __forceinline__ double2 tw_make(double re, double im, double*) { return make_double2(re, im); }
+
+// a * w, or a * conj(w) when CONJ
+template <bool CONJ = false>
+__device__ __forceinline__ float2 twmul(float2 a, float4 w) {
+    const float wy = CONJ ? -w.y : w.y, ww = CONJ ? -w.w : w.w;
+    return make_float2(fmaf(a.x, w.x, fmaf(-a.y, wy, fmaf(a.x, w.z, -a.y * ww))),
+                       fmaf(a.x, wy, fmaf(a.y, w.x, fmaf(a.x, ww, a.y * w.z))));
+}
+template <bool CONJ = false>
+__device__ __forceinline__ double2 twmul(double2 a, double2 w) {
+    return CONJ ? cmul(a, cconj(w)) : cmul(a, w);
+}
+// the hi part of a twiddle as a plain complex number (for the few places that need one)
+__device__ __forceinline__ float2 tw_hi(float4 w) { return make_float2(w.x, w.y); }
+__device__ __forceinline__ double2 tw_hi(double2 w) { return w; }
+
+// x * k for a constant k given in FP64: FP32 multiplies by fl(k) and adds x * fl(k - fl(k))
+template <typename T> __device__ __forceinline__ T kmul(T x, double k);
+template <> __device__ __forceinline__ double kmul<double>(double x, double k) { return x * k; }
+template <> __device__ __forceinline__ float kmul<float>(float x, double k) {
+    const float hi = (float)k, lo = (float)(k - (double)hi);
+    return fmaf(x, hi, x * lo);
+}
+// a * (c + i s) for FP64 constants c, s
+template <typename V> __device__ __forceinline__ V cmulk(V a, double c, double s) {
+    using T = decltype(V::x);
+    if constexpr (sizeof(T) == 8) {
+        return cmk<V>(a.x * c - a.y * s, a.x * s + a.y * c);
+    } else {
+        const float ch = (float)c, cl = (float)(c - (double)ch), sh = (float)s, sl = (float)(s - (double)sh);
+        return cmk<V>(fmaf(a.x, ch, fmaf(-a.y, sh, fmaf(a.x, cl, -a.y * sl))),
+                      fmaf(a.x, sh, fmaf(a.y, ch, fmaf(a.x, sl, a.y * cl))));
+    }
+}
+
 constexpr int kMaxStages = 16;
 constexpr int kThreads = 256;
 
@@ -119,8 +170,9 @@ template <typename T>
 struct Dev {
     const Film* films;
     const Plan* plans;
-    const cplx<T>* tw;
+    const tw_t<T>* tw;     // twiddle pool (hi + lo parts in the FP32 form)
     const T* lam;          // eigenvalue pool
+    const T* lam_lo;       // low parts of the eigenvalues (FP32 form), else null
     const T* dtab;         // dense DCT tables of short axes
     const T* ktab;         // -N_hat / (Px Py Pz), reduced real table
     T* const* field;       // device table: real field slot -> pool pointer

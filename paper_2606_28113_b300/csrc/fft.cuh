@@ -46,17 +46,17 @@ template <bool INV, typename V> struct Bfly<4, INV, V> {
 template <bool INV, typename V> struct Bfly<8, INV, V> {
     static __device__ __forceinline__ void run(V* a) {
         using T = decltype(V::x);
-        const T h = T(0.70710678118654752440);
+        constexpr double h = 0.70710678118654752440;
         V e[4] = {a[0], a[2], a[4], a[6]};
         V o[4] = {a[1], a[3], a[5], a[7]};
         Bfly<4, INV, V>::run(e);
         Bfly<4, INV, V>::run(o);
         // o[k] *= W8^k, W8 = exp(-+ i pi/4)
-        V o1 = INV ? cmk<V>(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
-                   : cmk<V>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+        V o1 = INV ? cmk<V>(kmul<T>(o[1].x - o[1].y, h), kmul<T>(o[1].x + o[1].y, h))
+                   : cmk<V>(kmul<T>(o[1].x + o[1].y, h), kmul<T>(o[1].y - o[1].x, h));
         V o2 = rot_i<INV>(o[2]);
-        V o3 = INV ? cmk<V>(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
-                   : cmk<V>(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+        V o3 = INV ? cmk<V>(-kmul<T>(o[3].x + o[3].y, h), kmul<T>(o[3].x - o[3].y, h))
+                   : cmk<V>(kmul<T>(o[3].y - o[3].x, h), -kmul<T>(o[3].x + o[3].y, h));
         a[0] = cadd(e[0], o[0]);
         a[4] = csub(e[0], o[0]);
         a[1] = cadd(e[1], o1);
@@ -71,8 +71,7 @@ template <bool INV, typename V> struct Bfly<8, INV, V> {
 template <bool INV, typename V> struct Bfly<16, INV, V> {
     // 16 = 4 x 4: DFT4 over m of a[r + 4m], twiddle W16^{rs}, DFT4 over r; X[s + 4t]
     static __device__ __forceinline__ void run(V* a) {
-        using T = decltype(V::x);
-        const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), h = T(0.70710678118654752440);
+        constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173, h = 0.70710678118654752440;
         V b[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -82,18 +81,16 @@ template <bool INV, typename V> struct Bfly<16, INV, V> {
             for (int s = 0; s < 4; ++s) b[r][s] = q[s];
         }
         // W16^k = (cos(2 pi k/16), -+ sin(2 pi k/16)) for k = r*s in {1,2,3,4,6,9}
-        const T sg = INV ? T(1) : T(-1);
-        const V w1 = cmk<V>(c1, sg * s1), w2 = cmk<V>(h, sg * h), w3 = cmk<V>(s1, sg * c1);
-        const V w6 = cmk<V>(-h, sg * h), w9 = cmk<V>(-c1, -sg * s1);
-        b[1][1] = cmul(b[1][1], w1);
-        b[1][2] = cmul(b[1][2], w2);
-        b[1][3] = cmul(b[1][3], w3);
-        b[2][1] = cmul(b[2][1], w2);
+        constexpr double sg = INV ? 1.0 : -1.0;
+        b[1][1] = cmulk(b[1][1], c1, sg * s1);
+        b[1][2] = cmulk(b[1][2], h, sg * h);
+        b[1][3] = cmulk(b[1][3], s1, sg * c1);
+        b[2][1] = cmulk(b[2][1], h, sg * h);
         b[2][2] = rot_i<INV>(b[2][2]);
-        b[2][3] = cmul(b[2][3], w6);
-        b[3][1] = cmul(b[3][1], w3);
-        b[3][2] = cmul(b[3][2], w6);
-        b[3][3] = cmul(b[3][3], w9);
+        b[2][3] = cmulk(b[2][3], -h, sg * h);
+        b[3][1] = cmulk(b[3][1], s1, sg * c1);
+        b[3][2] = cmulk(b[3][2], -h, sg * h);
+        b[3][3] = cmulk(b[3][3], -c1, -sg * s1);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             V q[4] = {b[0][s], b[1][s], b[2][s], b[3][s]};
@@ -107,10 +104,10 @@ template <bool INV, typename V> struct Bfly<16, INV, V> {
 template <bool INV, typename V> struct Bfly<3, INV, V> {
     static __device__ __forceinline__ void run(V* a) {
         using T = decltype(V::x);
-        const T s3 = T(0.86602540378443864676);   // sin(2 pi / 3)
+        constexpr double s3 = 0.86602540378443864676;   // sin(2 pi / 3)
         V s = cadd(a[1], a[2]), d = csub(a[1], a[2]);
         V t = cmk<V>(a[0].x - T(0.5) * s.x, a[0].y - T(0.5) * s.y);
-        V u = rot_i<INV>(cscale(d, s3));
+        V u = rot_i<INV>(cmk<V>(kmul<T>(d.x, s3), kmul<T>(d.y, s3)));
         a[0] = cadd(a[0], s);
         a[1] = cadd(t, u);
         a[2] = csub(t, u);
@@ -120,14 +117,14 @@ template <bool INV, typename V> struct Bfly<3, INV, V> {
 template <bool INV, typename V> struct Bfly<5, INV, V> {
     static __device__ __forceinline__ void run(V* a) {
         using T = decltype(V::x);
-        const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);   // cos(2pi/5), cos(4pi/5)
-        const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);    // sin(2pi/5), sin(4pi/5)
+        constexpr double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2pi/5), cos(4pi/5)
+        constexpr double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2pi/5), sin(4pi/5)
         V b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
         V d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
-        V t1 = cmk<V>(a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y);
-        V t2 = cmk<V>(a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y);
-        V u1 = rot_i<INV>(cmk<V>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
-        V u2 = rot_i<INV>(cmk<V>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+        V t1 = cmk<V>(a[0].x + kmul<T>(b1.x, c1) + kmul<T>(b2.x, c2), a[0].y + kmul<T>(b1.y, c1) + kmul<T>(b2.y, c2));
+        V t2 = cmk<V>(a[0].x + kmul<T>(b1.x, c2) + kmul<T>(b2.x, c1), a[0].y + kmul<T>(b1.y, c2) + kmul<T>(b2.y, c1));
+        V u1 = rot_i<INV>(cmk<V>(kmul<T>(d1.x, s1) + kmul<T>(d2.x, s2), kmul<T>(d1.y, s1) + kmul<T>(d2.y, s2)));
+        V u2 = rot_i<INV>(cmk<V>(kmul<T>(d1.x, s2) - kmul<T>(d2.x, s1), kmul<T>(d1.y, s2) - kmul<T>(d2.y, s1)));
         a[0] = cadd(a[0], cadd(b1, b2));
         a[1] = cadd(t1, u1);
         a[4] = csub(t1, u1);
@@ -139,7 +136,7 @@ template <bool INV, typename V> struct Bfly<5, INV, V> {
 // One Stockham stage of radix R over all lines: src -> dst.
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst,
-                                               int P, Lines L, int Ns, const cplx<T>* __restrict__ tw) {
+                                               int P, Lines L, int Ns, const tw_t<T>* __restrict__ tw) {
     using V = cplx<T>;
     const int nb = P / R;
     const int total = L.n * nb;
@@ -156,11 +153,7 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, 
         for (int t = 0; t < R; ++t) v[t] = s[(j + t * nb) * L.es];
         if (Ns > 1) {
 #pragma unroll
-            for (int t = 1; t < R; ++t) {
-                V w = tw[k * t * twstride];
-                if (INV) w = cconj(w);
-                v[t] = cmul(v[t], w);
-            }
+            for (int t = 1; t < R; ++t) v[t] = twmul<INV>(v[t], tw[k * t * twstride]);
         }
         Bfly<R, INV, V>::run(v);
         const int base = (j / Ns) * Ns * R + k;
@@ -172,7 +165,7 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ src, 
 // ---- compile-time Stockham for power-of-two lengths: all index arithmetic folds to shifts ----
 template <typename T, bool INV, int P, int R, int NS, bool CONTIG>
 __device__ __forceinline__ void ct_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, Lines L,
-                                         const cplx<T>* __restrict__ tw) {
+                                         const tw_t<T>* __restrict__ tw) {
     using V = cplx<T>;
     constexpr int NB = P / R;
     constexpr int TWS = P / (NS * R);
@@ -190,11 +183,7 @@ __device__ __forceinline__ void ct_stage(const cplx<T>* __restrict__ src, cplx<T
         for (int t = 0; t < R; ++t) v[t] = s[(j + t * NB) * es];
         if (NS > 1) {
 #pragma unroll
-            for (int t = 1; t < R; ++t) {
-                V w = tw[k * t * TWS];
-                if (INV) w = cconj(w);
-                v[t] = cmul(v[t], w);
-            }
+            for (int t = 1; t < R; ++t) v[t] = twmul<INV>(v[t], tw[k * t * TWS]);
         }
         Bfly<R, INV, V>::run(v);
         const int base = (j / NS) * NS * R + k;
@@ -207,7 +196,7 @@ __host__ __device__ constexpr int ct_radix(int rem) { return rem % 16 == 0 ? 16 
 
 template <typename T, bool INV, int P, int NS, bool CONTIG>
 struct CtFFT {
-    static __device__ __forceinline__ cplx<T>* run(cplx<T>* a, cplx<T>* b, Lines L, const cplx<T>* tw) {
+    static __device__ __forceinline__ cplx<T>* run(cplx<T>* a, cplx<T>* b, Lines L, const tw_t<T>* tw) {
         constexpr int R = ct_radix(P / NS);
         ct_stage<T, INV, P, R, NS, CONTIG>(a, b, L, tw);
         __syncthreads();
@@ -216,11 +205,11 @@ struct CtFFT {
 };
 template <typename T, bool INV, int P, bool CONTIG>
 struct CtFFT<T, INV, P, P, CONTIG> {
-    static __device__ __forceinline__ cplx<T>* run(cplx<T>* a, cplx<T>*, Lines, const cplx<T>*) { return a; }
+    static __device__ __forceinline__ cplx<T>* run(cplx<T>* a, cplx<T>*, Lines, const tw_t<T>*) { return a; }
 };
 
 template <typename T, bool INV, int P>
-__device__ __forceinline__ cplx<T>* ct_fft(cplx<T>* a, cplx<T>* b, Lines L, const cplx<T>* tw) {
+__device__ __forceinline__ cplx<T>* ct_fft(cplx<T>* a, cplx<T>* b, Lines L, const tw_t<T>* tw) {
     if (L.es == 1) return CtFFT<T, INV, P, 1, true>::run(a, b, L, tw);
     return CtFFT<T, INV, P, 1, false>::run(a, b, L, tw);
 }
@@ -233,7 +222,7 @@ __device__ __forceinline__ cplx<T>* ct_fft(cplx<T>* a, cplx<T>* b, Lines L, cons
 // TS: stride into the twiddle table (a table of W_{TS P} serves a P-point FFT with TS > 1)
 template <typename T, bool INV, int E, int TS = 1>
 __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* __restrict__ scr,
-                                              const cplx<T>* __restrict__ tw, int lane) {
+                                              const tw_t<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
     V v[E];
@@ -241,11 +230,7 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
     for (int k = 0; k < E; ++k) v[k] = a[lane + 32 * k];
     Bfly<E, INV, V>::run(v);
 #pragma unroll
-    for (int q = 1; q < E; ++q) {
-        V w = tw[TS * (lane * q)];
-        if (INV) w = cconj(w);
-        v[q] = cmul(v[q], w);
-    }
+    for (int q = 1; q < E; ++q) v[q] = twmul<INV>(v[q], tw[TS * (lane * q)]);
 #pragma unroll
     for (int q = 0; q < E; ++q) scr[q * 32 + (lane ^ ((q * G) & 31))] = v[q];
     __syncwarp();
@@ -255,23 +240,18 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
     Bfly<E, INV, V>::run(v);
     if (G > 1) {
 #pragma unroll
-        for (int s1 = 1; s1 < E; ++s1) {
-            V w = tw[TS * (E * g * s1)];
-            if (INV) w = cconj(w);
-            v[s1] = cmul(v[s1], w);
-        }
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = twmul<INV>(v[s1], tw[TS * (E * g * s1)]);
     }
 #pragma unroll
     for (int d = G / 2; d >= 1; d >>= 1) {
         const bool top = (g & d) == 0;
-        V w = tw[TS * ((P / (2 * d)) * (g % d))];
-        if (INV) w = cconj(w);
+        const tw_t<T> w = tw[TS * ((P / (2 * d)) * (g % d))];
 #pragma unroll
         for (int s1 = 0; s1 < E; ++s1) {
             V pv;
             pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
             pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
-            v[s1] = top ? cadd(v[s1], pv) : cmul(csub(pv, v[s1]), w);
+            v[s1] = top ? cadd(v[s1], pv) : twmul<INV>(csub(pv, v[s1]), w);
         }
     }
     const int s2 = G > 1 ? (int)(__brev((unsigned)g) >> (32 - __ffs(G) + 1)) : 0;
@@ -282,12 +262,12 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
 // Register-resident forward FFT of one line held by a warp: on entry v[k] = x[lane + 32k];
 // on exit v[s1] = X[q + E (s1 + E bitrev_G(g))] with q = lane / G, g = lane % G.
 template <typename T, int E>
-__device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const cplx<T>* __restrict__ tw, int lane) {
+__device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const tw_t<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
     Bfly<E, false, V>::run(v);
 #pragma unroll
-    for (int q = 1; q < E; ++q) v[q] = cmul(v[q], tw[lane * q]);
+    for (int q = 1; q < E; ++q) v[q] = twmul(v[q], tw[lane * q]);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < E; ++q) scr[q * 32 + (lane ^ ((q * G) & 31))] = v[q];
@@ -298,43 +278,43 @@ __device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ 
     Bfly<E, false, V>::run(v);
     if (G > 1) {
 #pragma unroll
-        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], tw[E * g * s1]);
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = twmul(v[s1], tw[E * g * s1]);
     }
 #pragma unroll
     for (int d = G / 2; d >= 1; d >>= 1) {
         const bool top = (g & d) == 0;
-        const V w = tw[(P / (2 * d)) * (g % d)];
+        const tw_t<T> w = tw[(P / (2 * d)) * (g % d)];
 #pragma unroll
         for (int s1 = 0; s1 < E; ++s1) {
             V pv;
             pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
             pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
-            v[s1] = top ? cadd(v[s1], pv) : cmul(csub(pv, v[s1]), w);
+            v[s1] = top ? cadd(v[s1], pv) : twmul(csub(pv, v[s1]), w);
         }
     }
 }
 
 // The adjoint of wreg_fwd: from the scrambled order back to v[k] = P * IDFT(X)[lane + 32k].
 template <typename T, int E>
-__device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const cplx<T>* __restrict__ tw, int lane) {
+__device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const tw_t<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
     const int q = lane / G, g = lane % G;
 #pragma unroll
     for (int d = 1; d <= G / 2; d <<= 1) {
         const bool top = (g & d) == 0;
-        const V w = cconj(tw[(P / (2 * d)) * (g % d)]);
+        const tw_t<T> w = tw[(P / (2 * d)) * (g % d)];   // used conjugated
 #pragma unroll
         for (int s1 = 0; s1 < E; ++s1) {
             V pv;
             pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
             pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
-            v[s1] = top ? cadd(v[s1], cmul(w, pv)) : csub(pv, cmul(w, v[s1]));
+            v[s1] = top ? cadd(v[s1], twmul<true>(pv, w)) : csub(pv, twmul<true>(v[s1], w));
         }
     }
     if (G > 1) {
 #pragma unroll
-        for (int s1 = 1; s1 < E; ++s1) v[s1] = cmul(v[s1], cconj(tw[E * g * s1]));
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = twmul<true>(v[s1], tw[E * g * s1]);
     }
     Bfly<E, true, V>::run(v);
     __syncwarp();
@@ -344,7 +324,7 @@ __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ 
 #pragma unroll
     for (int qq = 0; qq < E; ++qq) v[qq] = scr[qq * 32 + (lane ^ ((qq * G) & 31))];
 #pragma unroll
-    for (int qq = 1; qq < E; ++qq) v[qq] = cmul(v[qq], cconj(tw[lane * qq]));
+    for (int qq = 1; qq < E; ++qq) v[qq] = twmul<true>(v[qq], tw[lane * qq]);
     Bfly<E, true, V>::run(v);
 }
 
@@ -353,7 +333,7 @@ __device__ __forceinline__ int bitrev_lanes(int g, int G) {
 }
 
 template <typename T, bool INV, int E>
-__device__ __forceinline__ cplx<T>* warp_fft(cplx<T>* a, cplx<T>* b, Lines L, const cplx<T>* tw) {
+__device__ __forceinline__ cplx<T>* warp_fft(cplx<T>* a, cplx<T>* b, Lines L, const tw_t<T>* tw) {
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int line = threadIdx.x >> 5; line < L.n; line += nw)
         warp_fft_line<T, INV, E>(a + (long)line * L.ls, b + (long)line * L.ls, tw, lane);
@@ -366,8 +346,8 @@ __device__ __forceinline__ cplx<T>* warp_fft(cplx<T>* a, cplx<T>* b, Lines L, co
 // length 64..512 use the warp-per-line FFT; other power-of-two lengths up to 2048 the
 // compile-time Stockham; other lengths the generic mixed-radix Stockham.
 template <typename T, bool INV>
-__device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, const cplx<T>* __restrict__ twpool) {
-    const cplx<T>* tw = twpool + pl.tw;
+__device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, const tw_t<T>* __restrict__ twpool) {
+    const tw_t<T>* tw = twpool + pl.tw;
     if (L.es == 1 && L.ls >= pl.P) {
         switch (pl.P) {
             case 64: return warp_fft<T, INV, 2>(a, b, L, tw);
@@ -411,13 +391,13 @@ __device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, c
 
 // FFT of all lines with the length known at compile time (PC > 0), or the runtime path (PC = 0).
 template <typename T, bool INV, int PC>
-__device__ __forceinline__ cplx<T>* fft_lines_t(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, const cplx<T>* __restrict__ twpool) {
+__device__ __forceinline__ cplx<T>* fft_lines_t(cplx<T>* a, cplx<T>* b, Lines L, const Plan& pl, const tw_t<T>* __restrict__ twpool) {
     if constexpr (PC == 0) {
         return fft_lines<T, INV>(a, b, L, pl, twpool);
     } else if constexpr (PC == 1) {
         return a;
     } else {
-        const cplx<T>* tw = twpool + pl.tw;
+        const tw_t<T>* tw = twpool + pl.tw;
         if constexpr (PC >= 64 && PC <= 512) {
             if (L.es == 1 && L.ls >= PC) return warp_fft<T, INV, PC / 32>(a, b, L, tw);
         }
@@ -437,14 +417,14 @@ __device__ __forceinline__ int half_pos(int p, int k, int N) { return (2 * p + (
 // R: real lines (R.ls / R.es strides, length N).  ca, cb: complex scratch of >= ceil(L/2) * N.
 template <typename T, int PC = 0>
 __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const Plan& pl,
-                           const cplx<T>* __restrict__ twpool) {
+                           const tw_t<T>* __restrict__ twpool) {
     using V = cplx<T>;
     const int npair = (L.n + 1) / 2;
     if constexpr (PC >= 128 && PC <= 1024) {
         // the N-point FFT of each packed pair split by decimation in time into two N/2-point warp
         // FFTs (even and odd positions), so twice as many warps run half as long
         constexpr int H = PC / 2;
-        const V* tw = twpool + pl.tw;   // W_N; the half-length FFTs read it with stride 2
+        const tw_t<T>* tw = twpool + pl.tw;   // W_N; the half-length FFTs read it with stride 2
         for (int idx = threadIdx.x; idx < npair * PC; idx += blockDim.x) {
             int p = idx / PC, j = idx - p * PC;
             T re = R[(2 * p) * L.ls + j * L.es];
@@ -458,21 +438,21 @@ __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
                 warp_fft_line<T, false, H / 32, 2>(ca + line * H, cb + line * H, tw, lane);
             __syncthreads();
         }
-        const V* w4 = twpool + pl.tw4;
+        const tw_t<T>* w4 = twpool + pl.tw4;
         auto zat = [&](int p, int k) {   // Z[k] = E[k'] +- W_N^k' O[k'],  k' = k mod H
             const int k2 = k < H ? k : k - H;
-            const V e = ca[(2 * p) * H + k2], o = cmul(ca[(2 * p + 1) * H + k2], tw[k2]);
+            const V e = ca[(2 * p) * H + k2], o = twmul(ca[(2 * p + 1) * H + k2], tw[k2]);
             return k < H ? cadd(e, o) : csub(e, o);
         };
         for (int idx = threadIdx.x; idx < npair * PC; idx += blockDim.x) {
             int p = idx / PC, k = idx - p * PC;
             V Z = zat(p, k);
             V Zr = cconj(zat(p, k == 0 ? 0 : PC - k));
-            V w = w4[k];
+            const tw_t<T> w = w4[k];
             V va = cscale(cadd(Z, Zr), T(0.5));
             V vb = cscale(cmul_mi(csub(Z, Zr)), T(0.5));
-            R[(2 * p) * L.ls + k * L.es] = w.x * va.x - w.y * va.y;
-            if (2 * p + 1 < L.n) R[(2 * p + 1) * L.ls + k * L.es] = w.x * vb.x - w.y * vb.y;
+            R[(2 * p) * L.ls + k * L.es] = twmul(va, w).x;
+            if (2 * p + 1 < L.n) R[(2 * p + 1) * L.ls + k * L.es] = twmul(vb, w).x;
         }
         __syncthreads();
         return;
@@ -486,16 +466,16 @@ __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
     }
     __syncthreads();
     V* res = fft_lines_t<T, false, PC>(ca, cb, C, pl, twpool);
-    const V* w4 = twpool + pl.tw4;
+    const tw_t<T>* w4 = twpool + pl.tw4;
     for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
         int p = idx / N, k = idx - p * N;
         V Z = res[p * N + k];
         V Zr = cconj(res[p * N + (k == 0 ? 0 : N - k)]);
-        V w = w4[k];
+        const tw_t<T> w = w4[k];
         V va = cscale(cadd(Z, Zr), T(0.5));
         V vb = cscale(cmul_mi(csub(Z, Zr)), T(0.5));
-        R[(2 * p) * L.ls + k * L.es] = w.x * va.x - w.y * va.y;
-        if (2 * p + 1 < L.n) R[(2 * p + 1) * L.ls + k * L.es] = w.x * vb.x - w.y * vb.y;
+        R[(2 * p) * L.ls + k * L.es] = twmul(va, w).x;
+        if (2 * p + 1 < L.n) R[(2 * p + 1) * L.ls + k * L.es] = twmul(vb, w).x;
     }
     __syncthreads();
 }
@@ -503,31 +483,31 @@ __device__ void dct2_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
 // Inverse of dct2_lines up to a factor N (the caller folds 1/N into its scaling).
 template <typename T, int PC = 0>
 __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const Plan& pl,
-                           const cplx<T>* __restrict__ twpool) {
+                           const tw_t<T>* __restrict__ twpool) {
     using V = cplx<T>;
     const int npair = (L.n + 1) / 2;
     if constexpr (PC >= 128 && PC <= 1024) {
         // inverse N-point FFT split by decimation in frequency into two N/2-point warp FFTs:
         // z[2m] from C[k] + C[k+H], z[2m+1] from (C[k] - C[k+H]) conj(W_N^k)
         constexpr int H = PC / 2;
-        const V* tw = twpool + pl.tw;
-        const V* w4 = twpool + pl.tw4;
+        const tw_t<T>* tw = twpool + pl.tw;
+        const tw_t<T>* w4 = twpool + pl.tw4;
         auto cat = [&](int p, int k) {   // the packed pre-twiddled spectrum C[k] of pair p
             const bool hasb = (2 * p + 1 < L.n);
             T xa = R[(2 * p) * L.ls + k * L.es];
             T xar = (k == 0) ? T(0) : R[(2 * p) * L.ls + (PC - k) * L.es];
             T xb = hasb ? R[(2 * p + 1) * L.ls + k * L.es] : T(0);
             T xbr = (hasb && k != 0) ? R[(2 * p + 1) * L.ls + (PC - k) * L.es] : T(0);
-            V w = cconj(w4[k]);
-            V va = cmul(w, cmk<V>(xa, -xar));
-            V vb = cmul(w, cmk<V>(xb, -xbr));
+            const tw_t<T> w = w4[k];   // used conjugated
+            V va = twmul<true>(cmk<V>(xa, -xar), w);
+            V vb = twmul<true>(cmk<V>(xb, -xbr), w);
             return cmk<V>(va.x - vb.y, va.y + vb.x);
         };
         for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
             int p = idx / H, k = idx - p * H;
             const V c0 = cat(p, k), c1 = cat(p, k + H);
             ca[(2 * p) * H + k] = cadd(c0, c1);
-            ca[(2 * p + 1) * H + k] = cmul(csub(c0, c1), cconj(tw[k]));
+            ca[(2 * p + 1) * H + k] = twmul<true>(csub(c0, c1), tw[k]);
         }
         __syncthreads();
         {
@@ -547,7 +527,7 @@ __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
         return;
     }
     Lines C{npair, N, 1};
-    const V* w4 = twpool + pl.tw4;
+    const tw_t<T>* w4 = twpool + pl.tw4;
     for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
         int p = idx / N, k = idx - p * N;
         const bool hasb = (2 * p + 1 < L.n);
@@ -555,9 +535,9 @@ __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
         T xar = (k == 0) ? T(0) : R[(2 * p) * L.ls + (N - k) * L.es];
         T xb = hasb ? R[(2 * p + 1) * L.ls + k * L.es] : T(0);
         T xbr = (hasb && k != 0) ? R[(2 * p + 1) * L.ls + (N - k) * L.es] : T(0);
-        V w = cconj(w4[k]);
-        V va = cmul(w, cmk<V>(xa, -xar));
-        V vb = cmul(w, cmk<V>(xb, -xbr));
+        const tw_t<T> w = w4[k];   // used conjugated
+        V va = twmul<true>(cmk<V>(xa, -xar), w);
+        V vb = twmul<true>(cmk<V>(xb, -xbr), w);
         ca[p * N + k] = cmk<V>(va.x - vb.y, va.y + vb.x);
     }
     __syncthreads();
@@ -577,7 +557,7 @@ __device__ void dct3_lines(T* R, Lines L, int N, cplx<T>* ca, cplx<T>* cb, const
 // [pair][P]; extract line spectra with r2c_get.
 template <typename T, int PC = 0>
 __device__ cplx<T>* r2c_lines(const T* R, Lines L, int nlen, cplx<T>* ca, cplx<T>* cb, const Plan& pl,
-                              const cplx<T>* __restrict__ twpool) {
+                              const tw_t<T>* __restrict__ twpool) {
     using V = cplx<T>;
     const int P = pl.P;
     const int npair = (L.n + 1) / 2;
@@ -643,7 +623,7 @@ __device__ __forceinline__ void c2r_put_h(cplx<T>* ca, int p, int k, int P, cplx
 // N-point FFTs (plan pN); twP = W_P^m (m < P).  Returns the buffer holding the half layout.
 template <typename T, int N>
 __device__ cplx<T>* r2c_lines_h(const T* R, Lines L, int nlen, cplx<T>* ca, cplx<T>* cb, const Plan& pN,
-                                const cplx<T>* __restrict__ twpool, const cplx<T>* __restrict__ twP) {
+                                const tw_t<T>* __restrict__ twpool, const tw_t<T>* __restrict__ twP) {
     using V = cplx<T>;
     const int npair = (L.n + 1) / 2;
     for (int idx = threadIdx.x; idx < npair * N; idx += blockDim.x) {
@@ -654,7 +634,7 @@ __device__ cplx<T>* r2c_lines_h(const T* R, Lines L, int nlen, cplx<T>* ca, cplx
             if (2 * p + 1 < L.n) v.y = R[(2 * p + 1) * L.ls + n * L.es];
         }
         ca[(2 * p) * N + n] = v;
-        ca[(2 * p + 1) * N + n] = cmul(v, twP[n]);
+        ca[(2 * p + 1) * N + n] = twmul(v, twP[n]);
     }
     __syncthreads();
     return fft_lines_t<T, false, N>(ca, cb, Lines{2 * npair, N, 1}, pN, twpool);

@@ -65,7 +65,9 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
     const int y0 = wi.y, nrow = MULTI ? (wi.z > 0 ? wi.z : 1) : 1;
-    const int nx = F.nx, ny = F.ny, nz = F.nz, Px = F.Px, Pz = F.Pz, Kx = F.Kx;
+    // compile-time x lengths (NX >= 8) fold every index division by nx into a shift
+    const int nx = NX > 0 ? NX : F.nx, ny = F.ny, nz = F.nz;
+    const int Px = NX > 0 ? 2 * NX : F.Px, Pz = F.Pz, Kx = NX > 0 ? NX + 1 : F.Kx;
     const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0, ZTC);
     // the zero-padded x transform (Px = 2 NX) as two NX-point FFTs per line pair
     constexpr bool kHalfX = NX >= 64 && NX <= 512;
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         ppz = d.plans[F.splan_pz];
     }
     // staged twiddles: [W_nx | W4_nx | W_nz | W4_nz | W_Px | W_Pz], then the short-axis DCT tables
-    V* stw = reinterpret_cast<V*>(smem_raw);
+    tw_t<T>* stw = reinterpret_cast<tw_t<T>*>(smem_raw);
     {
         const int segs[6] = {F.gtw_dx, F.gtw4_dx, F.gtw_dz, F.gtw4_dz, F.gtw_px, F.gtw_pz};
         const int lens[6] = {nx, nx, nz, nz, stray ? Px : 0, stray ? Pz : 0};
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             off += lens[k];
         }
     }
-    V* xw0 = stw + Lo.tw;
+    V* xw0 = reinterpret_cast<V*>(stw + Lo.tw);
     V* xw1 = xw0 + Lo.xw;
     V* zw0 = xw1 + Lo.xw;
     V* zw1 = zw0 + Lo.zw;
@@ -117,13 +119,16 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         const int KC = Lo.kc;
         const int npx = (nz + 1) / 2;
         const int nxz = nx * nz;
-        const long long cbase = F.off_cell;
+        // in-film offsets are 32-bit; the film's base offsets are 64-bit
+        const long long cbase = F.off_cell + (long long)y * nx;
         const long long sbase = F.off_spec;
-        auto cell_of = [&](int z, int x) -> long long { return cbase + ((long long)z * ny + y) * nx + x; };
+        const int zstride = ny * nx;
+        auto cell_of = [&](int z, int x) -> long long { return cbase + (z * zstride + x); };
+        auto spec_of = [&](int kz, int kx) -> int { return (kz * ny + y) * Kx + kx; };
         const bool zreg = z_in_registers(nz);
         const T* Cz = sdt;                                       // DCT-II  C[k][n]
         const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
-        const V* twz = stw + ppz.tw;                             // W_Pz^m
+        const tw_t<T>* twz = stw + ppz.tw;                       // W_Pz^m
 
         // ---- phase R: right-hand sides and forward DCT ---------------------------------------
         for (int ci = 0; ci < pg.n_rhs; ++ci) {
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                         V hz[2 * kZReg];
     #pragma unroll
                         for (int kz = 0; kz < 2 * kZReg; ++kz)
-                            hz[kz] = kz < Pz ? H[((long long)kz * ny + y) * Kx + kx] : cmk<V>(T(0), T(0));
+                            hz[kz] = kz < Pz ? H[spec_of(kz, kx)] : cmk<V>(T(0), T(0));
                         if (zfft_reg<T, true>(hz, Pz)) {
     #pragma unroll
                             for (int z = 0; z < kZReg; ++z) acc[z] = hz[z];
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                                 int m = 0;
     #pragma unroll
                                 for (int z = 0; z < kZReg; ++z) {
-                                    if (z < nz) acc[z] = cadd(acc[z], cmul(hv, cconj(twz[m])));
+                                    if (z < nz) acc[z] = cadd(acc[z], twmul<true>(hv, twz[m]));
                                     m += kz;
                                     if (m >= Pz) m -= Pz;
                                 }
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     const int kcn = min(KC, Kx - kc0);
                     for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
                         int kz = idx / kcn, kc = idx - kz * kcn;
-                        zw0[kz * KC + kc] = H[((long long)kz * ny + y) * Kx + kc0 + kc];
+                        zw0[kz * KC + kc] = H[spec_of(kz, kc0 + kc)];
                     }
                     __syncthreads();
                     V* r = fft_lines<T, true>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
@@ -195,12 +200,12 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 }
                 if constexpr (kHalfX) {
                     // two NX-point inverse FFTs per pair; outputs n < nx only
-                    const V* twP = stw + ppx.tw;
+                    const tw_t<T>* twP = stw + ppx.tw;
                     V* r = fft_lines_t<T, true, NX>(xw0, xw1, Lines{2 * npx, NX, 1}, pdx, stw);
                     for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
                         int z = idx / nx, x = idx - z * nx;
                         const int p = z >> 1;
-                        const V v = cadd(r[(2 * p) * NX + x], cmul(r[(2 * p + 1) * NX + x], cconj(twP[x])));
+                        const V v = cadd(r[(2 * p) * NX + x], twmul<true>(r[(2 * p + 1) * NX + x], twP[x]));
                         h[idx] = (z & 1) ? v.y : v.x;
                     }
                 } else {
@@ -229,13 +234,17 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 const T* __restrict__ m2 = d.field[pg.state[1]];
                 const T* __restrict__ m3 = d.field[pg.state[2]];
                 const T* __restrict__ ma = d.field[pg.state[a]];
-                const T scale = T(pg.damp ? F.alpha * F.dt : F.dt);
-                const T eps = T(F.eps), Q = T(F.Q);
+                // dt (alpha dt), eps and the uniform applied field are split hi + lo in the FP32
+                // form: they set the precession rate in every step, so their FP32 rounding would
+                // act as a fixed perturbation of the parameters (lo parts are zero in FP64)
+                const double sd = pg.damp ? F.alpha * F.dt : F.dt;
+                const T sch = T(sd), scl = T(sd - (double)sch);
+                const T eph = T(F.eps), epl = T(F.eps - (double)eph), Q = T(F.Q);
                 const T ux = T(F.u[0]), uy = T(F.u[1]), uz = T(F.u[2]);
                 const T ua = T(F.u[a]);
                 const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
-                const T hea = T(F.he[a]);
-                const long long sz = (long long)nx * ny;
+                const T hea = T(F.he[a]), heal = T(F.he[a] - (double)hea);
+                const int sz = nx * ny;
                 // batches of kB cells per thread: every load of the batch is issued before any use
                 constexpr int kB = sizeof(T) == 4 ? 4 : 2;
                 for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
@@ -253,8 +262,8 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                         v3[u] = m3[c];
                         mc[u] = ma[c];
                         // neighbours with mirror ghosts (a missing neighbour repeats the cell)
-                        const long long o[6] = {x + 1 < nx ? 1 : 0, x > 0 ? -1 : 0, y + 1 < ny ? (long long)nx : 0,
-                                                y > 0 ? -(long long)nx : 0, z + 1 < nz ? sz : 0, z > 0 ? -sz : 0};
+                        const int o[6] = {x + 1 < nx ? 1 : 0, x > 0 ? -1 : 0, y + 1 < ny ? nx : 0,
+                                          y > 0 ? -nx : 0, z + 1 < nz ? sz : 0, z > 0 ? -sz : 0};
     #pragma unroll
                         for (int k = 0; k < 6; ++k) nb[u][k] = ma[c + o[k]];
                     }
@@ -269,8 +278,14 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                         for (int k = 0; k < 6; ++k) d6[k] = nb[u][k] - mc[u];
                         const T lap = ihx * (d6[0] + d6[1]) + ihy * (d6[2] + d6[3]) + ihz * (d6[4] + d6[5]);
                         const T he = d.he_cell ? d.he_cell[c * 3 + a] : hea;
+                        const T hel = d.he_cell ? T(0) : heal;
                         const T f = -Q * (mc[u] - mu * ua) + h[idx] + he;
-                        h[idx] = scale * (f + eps * lap);
+                        if constexpr (sizeof(T) == 8) {
+                            h[idx] = sch * (f + eph * lap);
+                        } else {
+                            const T x = f + fma(eph, lap, fma(epl, lap, hel));
+                            h[idx] = fma(sch, x, scl * x);
+                        }
                     }
                 }
             }
@@ -530,18 +545,18 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                         if (zfft_reg<T, false>(v, Pz)) {
     #pragma unroll
                             for (int kz = 0; kz < 2 * kZReg; ++kz)
-                                if (kz < Pz) out[((long long)kz * ny + y) * Kx + kx] = v[kz];
+                                if (kz < Pz) out[spec_of(kz, kx)] = v[kz];
                         } else {
                             for (int kz = 0; kz < Pz; ++kz) {
                                 V acc = cmk<V>(T(0), T(0));
                                 int m = 0;
     #pragma unroll
                                 for (int z = 0; z < kZReg; ++z) {
-                                    if (z < nz) acc = cadd(acc, cmul(v[z], twz[m]));
+                                    if (z < nz) acc = cadd(acc, twmul(v[z], twz[m]));
                                     m += kz;
                                     if (m >= Pz) m -= Pz;
                                 }
-                                out[((long long)kz * ny + y) * Kx + kx] = acc;
+                                out[spec_of(kz, kx)] = acc;
                             }
                         }
                     }
@@ -557,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                     V* q = fft_lines<T, false>(zw0, zw1, Lines{kcn, 1, KC}, ppz, stw);
                     for (int idx = threadIdx.x; idx < Pz * kcn; idx += blockDim.x) {
                         int kz = idx / kcn, kc = idx - kz * kcn;
-                        out[((long long)kz * ny + y) * Kx + kc0 + kc] = q[kz * KC + kc];
+                        out[spec_of(kz, kc0 + kc)] = q[kz * KC + kc];
                     }
                     __syncthreads();
                 }
@@ -584,10 +599,10 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
     const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
     const int kz = wi.y, kx0 = wi.z, tn = wi.w;
-    const int nx = F.nx, ny = F.ny, nz = F.nz;
+    const int nx = F.nx, ny = NY > 0 ? NY : F.ny, nz = F.nz;
     __shared__ Plan pdy;
     if (threadIdx.x == 0) pdy = d.plans[F.splan_dy];   // staged copy: twiddles at 0, quarter-wave at ny
-    V* stw = reinterpret_cast<V*>(smem_raw);
+    tw_t<T>* stw = reinterpret_cast<tw_t<T>*>(smem_raw);
     for (int i = threadIdx.x; i < ny; i += blockDim.x) {
         stw[i] = d.tw[F.gtw_dy + i];
         stw[ny + i] = d.tw[F.gtw4_dy + i];
@@ -595,33 +610,61 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
     __syncthreads();
     pdl_wait();
     const int npair = (tn + 1) / 2;
-    V* c0 = stw + 2 * ny;
+    V* c0 = reinterpret_cast<V*>(stw + 2 * ny);
     V* c1 = c0 + npair * ny;
     T* R = reinterpret_cast<T*>(c1 + npair * ny);
     const int LR = ny + 8;   // padded line stride: tile copies hit distinct banks
-    const T c = T(pg.damp ? F.alpha * F.eps : F.eps) * T(F.dt);
+    // tile copies: thread -> column t_ld of rows y_ld, y_ld + rpp, ... (no per-element division)
+    const int rpp = (int)blockDim.x / tn;
+    const int t_ld = (int)threadIdx.x % tn, y_ld = (int)threadIdx.x / tn;
+    const bool ld_on = y_ld < rpp;
+    // eigen-scale 1 / (N (1 + c (lx + ly + lz))), c = eps dt (alpha eps dt for Step 2); in the
+    // FP32 form c, 1/N and the eigenvalues are double-float so that the scale, which is applied
+    // to every mode in every solve, carries no fixed table rounding
+    const double cd = (pg.damp ? F.alpha * F.eps : F.eps) * F.dt;
+    const double nd = 1.0 / ((double)nx * ny * nz);
+    const T ch = T(cd), cl = T(cd - (double)ch), nh = T(nd), nl = T(nd - (double)nh);
     const T* lx = d.lam + F.lam;
     const T* ly = lx + nx;
-    const T lzv = (lx + nx + ny)[kz];
-    const T norm = T(1.0 / ((double)nx * ny * nz));
+    const T lzh = ly[ny + kz];
+    const T* lxl = d.lam_lo ? d.lam_lo + F.lam : nullptr;
+    const T lzl = lxl ? lxl[nx + ny + kz] : T(0);
     for (int f = 0; f < pg.n; ++f) {
         T* g = d.field[pg.slot[f]] + F.off_cell + (long long)kz * ny * nx + kx0;
-        for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
-            int yy = idx / tn, t = idx - yy * tn;
-            R[t * LR + yy] = g[(long long)yy * nx + t];
-        }
+        if (ld_on)
+            for (int yy = y_ld; yy < ny; yy += rpp) R[t_ld * LR + yy] = g[yy * nx + t_ld];
         __syncthreads();
         dct2_lines<T, NY>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
         for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
-            int t = idx / ny, ky = idx - t * ny;
-            R[t * LR + ky] *= norm / (T(1) + c * (lx[kx0 + t] + ly[ky] + lzv));
+            const int t = idx / ny, ky = idx - t * ny;
+            T& r = R[t * LR + ky];
+            if constexpr (sizeof(T) == 8) {
+                r *= nh / (T(1) + ch * (lx[kx0 + t] + ly[ky] + lzh));
+            } else {
+                // Lambda = lx + ly + lz, s = 1 + c Lambda, scale = (1/N) / s, all double-float
+                T a, e1, Lh, e2;
+                two_sum(lx[kx0 + t], ly[ky], a, e1);
+                two_sum(a, lzh, Lh, e2);
+                const T Ll = e1 + e2 + (lxl[kx0 + t] + lxl[nx + ky] + lzl);
+                T p, pe;
+                two_prod(ch, Lh, p, pe);
+                const T pl = pe + fma(ch, Ll, cl * Lh);
+                T sh, se;
+                two_sum(T(1), p, sh, se);
+                const T sl = se + pl;
+                const T r0 = T(1) / sh;
+                const T res = fma(-sh, r0, T(1)) - sl * r0;   // 1 - s r0
+                const T ih = r0, il = r0 * res;
+                T q, qe;
+                two_prod(nh, ih, q, qe);
+                const T ql = qe + fma(nh, il, nl * ih);
+                r = fma(r, q, r * ql);
+            }
         }
         __syncthreads();
         dct3_lines<T, NY>(R, Lines{tn, LR, 1}, ny, c0, c1, pdy, stw);
-        for (int idx = threadIdx.x; idx < ny * tn; idx += blockDim.x) {
-            int yy = idx / tn, t = idx - yy * tn;
-            g[(long long)yy * nx + t] = R[t * LR + yy];
-        }
+        if (ld_on)
+            for (int yy = y_ld; yy < ny; yy += rpp) g[yy * nx + t_ld] = R[t_ld * LR + yy];
         __syncthreads();
     }
 }
@@ -644,14 +687,14 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
     __shared__ Plan ppy;
     if (threadIdx.x == 0) ppy = d.plans[F.plan_py];
     __syncthreads();
-    V* stw = reinterpret_cast<V*>(smem_raw);
+    tw_t<T>* stw = reinterpret_cast<tw_t<T>*>(smem_raw);
     stage_plan<T>(ppy, d.tw, stw, 0, false);
     __syncthreads();
     if (threadIdx.x == 0) ppy.tw = 0;
     __syncthreads();
     const int LS = Py + 4;   // padded line stride: tile copies hit distinct banks
     const int B = tx * LS;
-    V* w0 = stw + Py;
+    V* w0 = reinterpret_cast<V*>(stw + Py);
     V* w1 = w0 + B;
     V* acc = w1 + B;     // pg.n accumulators
     const int HyP = ktab_row(Py), Hz = Pz / 2 + 1;
@@ -747,12 +790,12 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     const int ny = F.ny, Kx = F.Kx, Pz = F.Pz, Hz = Pz / 2 + 1;
     const int kzr = kz <= Pz - kz ? kz : Pz - kz;
     const bool zodd = kz > Pz / 2;
-    V* stw = reinterpret_cast<V*>(smem_raw);
-    V* scr0 = stw + P;
+    tw_t<T>* stw = reinterpret_cast<tw_t<T>*>(smem_raw);
+    V* scr0 = reinterpret_cast<V*>(stw + P);
     V* inb = scr0 + kWarpLines * P;                                       // [3][lines][LI]
     T* kbuf = reinterpret_cast<T*>(inb + 3 * kWarpLines * LI);            // [3 NOUT][lines][HyP]
     {
-        const V* g = d.tw + d.plans[F.plan_py].tw;
+        const tw_t<T>* g = d.tw + d.plans[F.plan_py].tw;
         for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = g[i];
     }
     pdl_wait();

@@ -53,13 +53,14 @@ __host__ __device__ inline XZLayout xz_layout(int nx, int nz, int Px, int Pz, in
 
 template <typename T>
 __host__ __device__ inline size_t xz_smem_bytes(const XZLayout& L) {
-    return (size_t)(L.tw + 2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)(3 * L.slab + L.dt) * sizeof(T) + (size_t)L.tc;
+    return (size_t)L.tw * sizeof(tw_t<T>) + (size_t)(2 * L.xw + 2 * L.zw) * sizeof(cplx<T>) + (size_t)(3 * L.slab + L.dt) * sizeof(T) +
+           (size_t)L.tc;
 }
 
 // Copy the twiddle tables of `pl` (W_P, and the DCT quarter-wave table when `dct`) from the
 // global pool to shared memory at `stw + off`, and point the plan at the staged copy.
 template <typename T>
-__device__ __forceinline__ void stage_plan(Plan& pl, const cplx<T>* __restrict__ g, cplx<T>* stw, int off, bool dct) {
+__device__ __forceinline__ void stage_plan(Plan& pl, const tw_t<T>* __restrict__ g, tw_t<T>* stw, int off, bool dct) {
     const int P = pl.P;
     for (int i = threadIdx.x; i < P; i += blockDim.x) stw[off + i] = g[pl.tw + i];
     if (dct)
@@ -76,7 +77,7 @@ __host__ __device__ inline long long ktab_index(int c, int kx, int kzr, int kyr,
 }
 
 // Register stray pass (one warp per kx line, Py = 32 E): shared-memory layout of one CTA of
-// kWarpLines lines.  Complex: [W_Py | scratch per warp (Py) | staged input lines 3 x lines x LI];
+// kWarpLines lines.  Twiddles W_Py; complex: [scratch per warp (Py) | staged input lines 3 x lines x LI];
 // real: staged table lines [3 NOUT][lines][HyP].  LI = Py/2 + 8 makes the asynchronous copies of
 // a (y, kx) tile land two lanes per bank (the minimum for 8-byte elements).
 constexpr int kWarpLines = 4;   // kx lines (warps) per CTA of the register stray pass
@@ -85,7 +86,7 @@ __host__ __device__ inline int yw_line_stride(int Py) { return Py / 2 + 8; }
 
 template <typename T>
 __host__ __device__ inline size_t yw_smem_bytes(int Py, int nout) {
-    return (size_t)(Py + kWarpLines * Py + 3 * kWarpLines * yw_line_stride(Py)) * sizeof(cplx<T>) +
+    return (size_t)Py * sizeof(tw_t<T>) + (size_t)(kWarpLines * Py + 3 * kWarpLines * yw_line_stride(Py)) * sizeof(cplx<T>) +
            (size_t)3 * nout * kWarpLines * ktab_row(Py) * sizeof(T);
 }
 
