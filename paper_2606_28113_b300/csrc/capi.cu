@@ -214,6 +214,14 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
 // ---- size-class dispatch ---------------------------------------------------------------------
 static int pow2_key(int n, int lo, int hi) { return (n >= lo && n <= hi && (n & (n - 1)) == 0) ? n : 0; }
 
+// slab-pass size class of a film: its x length when that is a power of two in 8..512 and the
+// film starts at a pool offset that is a multiple of four cells (the compile-time kernels move
+// four cells per access), else 0 (runtime x length); the FP64 form uses the runtime kernel only
+static int xz_key(bool fp64, const Film& F) {
+    if (fp64 || F.off_cell % 4 != 0) return 0;
+    return pow2_key(F.nx, 8, 512);
+}
+
 // size classes whose slab pass runs the tensor-core z transforms in the TF32X3 form
 static bool ztc_class(bool tf32x3, int key) { return tf32x3 && (key == 128 || key == 256 || key == 512); }
 
@@ -222,6 +230,33 @@ constexpr int kMaxRowsPerCTA = 8;   // slab pass packing: y rows of one film per
 // size classes whose slab pass may pack several y rows per CTA (FP32 form; small slabs)
 static bool packable_class(bool fp64, bool tf32x3, int key) {
     return !fp64 && !ztc_class(tf32x3, key) && key <= 256;
+}
+
+// launch type of a slab program: 1 right-hand sides only, 2 Gauss-Seidel update, 3 damping update
+// and projection (the step's programs), 0 anything else (energy, set-up and adjoint programs)
+static int xz_mode(const XZProg& p) {
+    if (p.n_rhs > 0 && p.n_inv == 0 && p.op == 0 && p.n_fwd == 0 && p.rhs_dct) {
+        for (int i = 0; i < p.n_rhs; ++i)
+            if (p.rhs_copy[i] >= 0 || p.rhs_hs_store[i] >= 0) return 0;
+        return 1;
+    }
+    if (p.n_rhs == 0 && p.op == 1) return 2;
+    if (p.n_rhs == 0 && p.op == 2) return 3;
+    return 0;
+}
+
+// compile-time x lengths with launch-type kernels (single row per CTA, FP32, no tensor cores)
+static bool mode_class(int key) { return key == 64 || key == 128 || key == 256 || key == 512; }
+
+template <typename T, int K>
+static void launch_xz_mode(int mode, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg,
+                           int stray) {
+    switch (mode) {
+        case 1: xz_go<T, K, false, false, 1>(nb, smem, st, d, w, pg, stray); break;
+        case 2: xz_go<T, K, false, false, 2>(nb, smem, st, d, w, pg, stray); break;
+        case 3: xz_go<T, K, false, false, 3>(nb, smem, st, d, w, pg, stray); break;
+        default: xz_go<T, K, false, false, 0>(nb, smem, st, d, w, pg, stray); break;
+    }
 }
 
 template <typename T>
@@ -246,9 +281,17 @@ static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T
                 default: xz_go<T, 512, true, false>(nb, smem, st, d, w, pg, stray); return;
             }
         }
+        const int mode = xz_mode(pg);
+        switch (key) {
+            case 64: launch_xz_mode<T, 64>(mode, nb, smem, st, d, w, pg, stray); return;
+            case 128: launch_xz_mode<T, 128>(mode, nb, smem, st, d, w, pg, stray); return;
+            case 256: launch_xz_mode<T, 256>(mode, nb, smem, st, d, w, pg, stray); return;
+            case 512: launch_xz_mode<T, 512>(mode, nb, smem, st, d, w, pg, stray); return;
+            default: break;
+        }
         switch (key) {
 #define SGSPM_XZ(K) case K: xz_go<T, K, false, false>(nb, smem, st, d, w, pg, stray); break;
-            SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32) SGSPM_XZ(64) SGSPM_XZ(128) SGSPM_XZ(256) SGSPM_XZ(512)
+            SGSPM_XZ(8) SGSPM_XZ(16) SGSPM_XZ(32)
 #undef SGSPM_XZ
             default: xz_go<T, 0, false, false>(nb, smem, st, d, w, pg, stray);
         }
@@ -285,6 +328,20 @@ static cudaError_t attr_xz(int key, size_t smem, bool tf32x3) {
                 case 256: return xz_attr<T, 256, true, false>(smem);
                 default: return xz_attr<T, 512, true, false>(smem);
             }
+        }
+        if (mode_class(key)) {
+            cudaError_t e = cudaSuccess;
+            switch (key) {
+#define SGSPM_XZM(K)                                                                                         \
+    case K:                                                                                                  \
+        e = xz_attr<T, K, false, false, 1>(smem);                                                            \
+        if (e == cudaSuccess) e = xz_attr<T, K, false, false, 2>(smem);                                      \
+        if (e == cudaSuccess) e = xz_attr<T, K, false, false, 3>(smem);                                      \
+        break;
+                SGSPM_XZM(64) SGSPM_XZM(128) SGSPM_XZM(256) SGSPM_XZM(512)
+#undef SGSPM_XZM
+            }
+            if (e != cudaSuccess) return e;
         }
         switch (key) {
 #define SGSPM_XZ(K) case K: return xz_attr<T, K, false, false>(smem);
@@ -1168,7 +1225,7 @@ static int setup_t(sgspm_ctx* ctx) {
     size_t sx = 0, sy = 0;
     int maxPy = 1, maxny = 1;
     for (const Film& F : ctx->films) {
-        const int key = sizeof(T) == 8 ? 0 : pow2_key(F.nx, 8, 512);
+        const int key = xz_key(sizeof(T) == 8, F);
         XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray, ztc_class(ctx->tf32x3, key));
         size_t b = xz_smem_bytes<T>(L);
         if (b > sx) sx = b;
@@ -1206,7 +1263,7 @@ static int setup_t(sgspm_ctx* ctx) {
         std::map<int, size_t> sxk;
         for (int f = 0; f < ctx->nfilm; ++f) {
             const Film& F = ctx->films[f];
-            const int kx = sizeof(T) == 8 ? 0 : pow2_key(F.nx, 8, 512);
+            const int kx = xz_key(sizeof(T) == 8, F);
             for (int y = 0; y < F.ny; ++y) wx[kx].push_back(make_int4(f, y, 0, 0));
             XZLayout L = xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray, ztc_class(ctx->tf32x3, kx));
             sxk[kx] = std::max(sxk[kx], xz_smem_bytes<T>(L));
@@ -1717,7 +1774,7 @@ int sgspm_step(sgspm_t ctx, long long n) {
 }
 
 // ---- batch packing and its autotuner ----------------------------------------------------------
-static int xz_class_key(const sgspm_ctx* ctx, const Film& F) { return ctx->fp64 ? 0 : pow2_key(F.nx, 8, 512); }
+static int xz_class_key(const sgspm_ctx* ctx, const Film& F) { return xz_key(ctx->fp64, F); }
 
 // Rebuild the slab-pass work list of class c with `rows` y rows per CTA.
 static int set_class_rows(sgspm_ctx* ctx, size_t c, int rows) {

@@ -49,6 +49,16 @@ template <bool CONJ = false>
 __device__ __forceinline__ double2 twmul(double2 a, double2 w) {
     return CONJ ? cmul(a, cconj(w)) : cmul(a, w);
 }
+// a * w (or a * conj(w)) with the full double-float twiddle when LO, else with its hi part only
+template <bool CONJ, bool LO, typename V, typename W>
+__device__ __forceinline__ V twmul_p(V a, W w) {
+    if constexpr (LO) {
+        return twmul<CONJ>(a, w);
+    } else {
+        const V h = cmk<V>(w.x, CONJ ? -w.y : w.y);
+        return cmul(a, h);
+    }
+}
 // the hi part of a twiddle as a plain complex number (for the few places that need one)
 __device__ __forceinline__ float2 tw_hi(float4 w) { return make_float2(w.x, w.y); }
 __device__ __forceinline__ double2 tw_hi(double2 w) { return w; }

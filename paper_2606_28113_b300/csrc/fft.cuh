@@ -261,13 +261,13 @@ __device__ __forceinline__ void warp_fft_line(cplx<T>* __restrict__ a, cplx<T>* 
 
 // Register-resident forward FFT of one line held by a warp: on entry v[k] = x[lane + 32k];
 // on exit v[s1] = X[q + E (s1 + E bitrev_G(g))] with q = lane / G, g = lane % G.
-template <typename T, int E>
+template <typename T, int E, bool LO = true>
 __device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const tw_t<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
     Bfly<E, false, V>::run(v);
 #pragma unroll
-    for (int q = 1; q < E; ++q) v[q] = twmul(v[q], tw[lane * q]);
+    for (int q = 1; q < E; ++q) v[q] = twmul_p<false, LO>(v[q], tw[lane * q]);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < E; ++q) scr[q * 32 + (lane ^ ((q * G) & 31))] = v[q];
@@ -278,7 +278,7 @@ __device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ 
     Bfly<E, false, V>::run(v);
     if (G > 1) {
 #pragma unroll
-        for (int s1 = 1; s1 < E; ++s1) v[s1] = twmul(v[s1], tw[E * g * s1]);
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = twmul_p<false, LO>(v[s1], tw[E * g * s1]);
     }
 #pragma unroll
     for (int d = G / 2; d >= 1; d >>= 1) {
@@ -289,13 +289,13 @@ __device__ __forceinline__ void wreg_fwd(cplx<T> (&v)[E], cplx<T>* __restrict__ 
             V pv;
             pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
             pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
-            v[s1] = top ? cadd(v[s1], pv) : twmul(csub(pv, v[s1]), w);
+            v[s1] = top ? cadd(v[s1], pv) : twmul_p<false, LO>(csub(pv, v[s1]), w);
         }
     }
 }
 
 // The adjoint of wreg_fwd: from the scrambled order back to v[k] = P * IDFT(X)[lane + 32k].
-template <typename T, int E>
+template <typename T, int E, bool LO = true>
 __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ scr, const tw_t<T>* __restrict__ tw, int lane) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
@@ -309,12 +309,12 @@ __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ 
             V pv;
             pv.x = __shfl_xor_sync(0xffffffffu, v[s1].x, d);
             pv.y = __shfl_xor_sync(0xffffffffu, v[s1].y, d);
-            v[s1] = top ? cadd(v[s1], twmul<true>(pv, w)) : csub(pv, twmul<true>(v[s1], w));
+            v[s1] = top ? cadd(v[s1], twmul_p<true, LO>(pv, w)) : csub(pv, twmul_p<true, LO>(v[s1], w));
         }
     }
     if (G > 1) {
 #pragma unroll
-        for (int s1 = 1; s1 < E; ++s1) v[s1] = twmul<true>(v[s1], tw[E * g * s1]);
+        for (int s1 = 1; s1 < E; ++s1) v[s1] = twmul_p<true, LO>(v[s1], tw[E * g * s1]);
     }
     Bfly<E, true, V>::run(v);
     __syncwarp();
@@ -324,7 +324,7 @@ __device__ __forceinline__ void wreg_adj(cplx<T> (&v)[E], cplx<T>* __restrict__ 
 #pragma unroll
     for (int qq = 0; qq < E; ++qq) v[qq] = scr[qq * 32 + (lane ^ ((qq * G) & 31))];
 #pragma unroll
-    for (int qq = 1; qq < E; ++qq) v[qq] = twmul<true>(v[qq], tw[lane * qq]);
+    for (int qq = 1; qq < E; ++qq) v[qq] = twmul_p<true, LO>(v[qq], tw[lane * qq]);
     Bfly<E, true, V>::run(v);
 }
 

@@ -25,10 +25,10 @@ static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, 
 }
 
 // XZ slab pass: NX compile-time x length (0: runtime), ZTC tensor-core z transforms, MULTI
-// several y rows per CTA.
-template <typename T, int NX, bool ZTC, bool MULTI>
+// several y rows per CTA, MODE launch type (0 generic, 1 rhs, 2 Gauss-Seidel, 3 final).
+template <typename T, int NX, bool ZTC, bool MULTI, int MODE = 0>
 void xz_go(unsigned nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray);
-template <typename T, int NX, bool ZTC, bool MULTI>
+template <typename T, int NX, bool ZTC, bool MULTI, int MODE = 0>
 cudaError_t xz_attr(size_t smem);
 // static shared memory of the variant's kernel (bytes), or a CUDA error as a negative value
 template <typename T, int NX, bool ZTC, bool MULTI>

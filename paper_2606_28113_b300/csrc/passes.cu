@@ -50,6 +50,66 @@ __device__ __forceinline__ bool zfft_reg(cplx<T> (&v)[2 * kZReg], int P) {
     }
 }
 
+// m^{n+1} = m*** / |m***| for a double-float m*** = h + l (Step 3): |m***|^2 in double-float, its
+// inverse square root by one double-float Newton step from rsqrt.  Returns false (and the
+// unnormalised m***) if |m***| is zero or not finite.
+template <typename T>
+__device__ __forceinline__ bool project_df(const T (&h)[3], const T (&l)[3], T (&oh)[3], T (&ol)[3]) {
+    T p0, e0, p1, e1, p2, e2;
+    two_prod(h[0], h[0], p0, e0);
+    two_prod(h[1], h[1], p1, e1);
+    two_prod(h[2], h[2], p2, e2);
+    T s1, f1, n2h, f2;
+    two_sum(p0, p1, s1, f1);
+    two_sum(s1, p2, n2h, f2);
+    T n2l = f1 + f2 + e0 + e1 + e2 + T(2) * (h[0] * l[0] + h[1] * l[1] + h[2] * l[2]);
+    T nh, nl;
+    fast_two_sum(n2h, n2l, nh, nl);
+    bool ok = true;
+    if (!(nh > T(0)) || !isfinite(nh)) {
+        ok = false;
+        nh = T(1);
+        nl = T(0);
+    }
+    const T r0 = rsqrt(nh);
+    T q, qe, a, ae;
+    two_prod(r0, r0, q, qe);
+    two_prod(nh, q, a, ae);
+    const T rho = ((T(1) - a) - ae) - (nh * qe + nl * q);
+    const T cc = T(0.5) * r0 * rho;   // 1/|m***| = r0 + cc
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T pp, pe;
+        two_prod(h[i], r0, pp, pe);
+        fast_two_sum(pp, pe + (h[i] * cc + l[i] * r0), oh[i], ol[i]);
+    }
+    return ok;
+}
+
+// ---- four-cell row access (compile-time x lengths, FP32) ------------------------------------
+// A slab is nz lines of NX cells: in shared memory with line stride NX, in a field at row base
+// g (the film's cell offset plus y nx, 16-byte aligned: films of these size classes start at
+// pool offsets that are multiples of four) with line stride zs.  Each access moves four cells.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+template <int NX>
+__device__ __forceinline__ void slab_load4(float* s, const float* __restrict__ g, int nz, int zs) {
+    constexpr int N4 = NX / 4;
+    for (int i = threadIdx.x; i < nz * N4; i += blockDim.x) {
+        const int z = i / N4, x4 = i - z * N4;
+        st4(s + 4 * i, ld4(g + z * zs + 4 * x4));
+    }
+}
+template <int NX>
+__device__ __forceinline__ void slab_store4(float* __restrict__ g, const float* s, int nz, int zs) {
+    constexpr int N4 = NX / 4;
+    for (int i = threadIdx.x; i < nz * N4; i += blockDim.x) {
+        const int z = i / N4, x4 = i - z * N4;
+        st4(g + z * zs + 4 * x4, ld4(s + 4 * i));
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // XZ slab pass
 // ------------------------------------------------------------------------------------------
@@ -57,7 +117,11 @@ __device__ __forceinline__ bool zfft_reg(cplx<T> (&v)[2 * kZReg], int P) {
 // ZTC: TF32X3 form (FP32 only): the z transforms of films with tc_zdct_ok run on the tensor cores
 // MULTI: a work item covers rows y0 .. y0 + w - 1 of one film (packing of small slabs); the
 //        single-row kernels keep the loop at one compile-time trip
-template <typename T, int NX, bool ZTC = false, bool MULTI = false>
+// MODE: 0 runs whatever the program asks for; 1 (right-hand sides), 2 (Gauss-Seidel update) and
+//       3 (damping update and projection) compile only the phases of that launch type, so that a
+//       launch fetches and caches far less code (the generic kernel's instruction stream is its
+//       largest stall)
+template <typename T, int NX, bool ZTC = false, bool MULTI = false, int MODE = 0>
 __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -71,6 +135,8 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0, ZTC);
     // the zero-padded x transform (Px = 2 NX) as two NX-point FFTs per line pair
     constexpr bool kHalfX = NX >= 64 && NX <= 512;
+    // four-cell loads and stores of the pointwise phases (FP32, compile-time x length)
+    constexpr bool kVec = NX >= 8 && sizeof(T) == 4;
     __shared__ Plan pdx, pdz, ppx, ppz;
     if (threadIdx.x == 0) {
         // pre-staged plan copies (their twiddle offsets refer to the shared layout below)
@@ -125,22 +191,39 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         const int zstride = ny * nx;
         auto cell_of = [&](int z, int x) -> long long { return cbase + (z * zstride + x); };
         auto spec_of = [&](int kz, int kx) -> int { return (kz * ny + y) * Kx + kx; };
+        // slab <-> field row copies
+        auto load_slab = [&](T* sl, const T* __restrict__ f) {
+            if constexpr (kVec) {
+                slab_load4<NX>(sl, f + cbase, nz, zstride);
+            } else {
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                    const int z = idx / nx, x = idx - z * nx;
+                    sl[idx] = f[cell_of(z, x)];
+                }
+            }
+        };
+        auto store_slab = [&](T* __restrict__ f, const T* sl) {
+            if constexpr (kVec) {
+                slab_store4<NX>(f + cbase, sl, nz, zstride);
+            } else {
+                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                    const int z = idx / nx, x = idx - z * nx;
+                    f[cell_of(z, x)] = sl[idx];
+                }
+            }
+        };
         const bool zreg = z_in_registers(nz);
         const T* Cz = sdt;                                       // DCT-II  C[k][n]
         const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
         const tw_t<T>* twz = stw + ppz.tw;                       // W_Pz^m
 
         // ---- phase R: right-hand sides and forward DCT ---------------------------------------
-        for (int ci = 0; ci < pg.n_rhs; ++ci) {
+        for (int ci = 0; (MODE == 0 || MODE == 1) && ci < pg.n_rhs; ++ci) {
             const int a = pg.rhs_comp[ci];
             T* h = slabs;   // slab 0
-            if (pg.rhs_copy[ci] >= 0) {
+            if (MODE == 0 && pg.rhs_copy[ci] >= 0) {
                 // the right-hand side is given (adjoint solves): copy it and transform
-                const T* src = d.field[pg.rhs_copy[ci]];
-                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                    int z = idx / nx, x = idx - z * nx;
-                    h[idx] = src[cell_of(z, x)];
-                }
+                load_slab(h, d.field[pg.rhs_copy[ci]]);
                 __syncthreads();
             } else if (pg.rhs_h[ci] >= 0 && stray) {
                 const V* H = d.spec[pg.rhs_h[ci]] + sbase;
@@ -220,16 +303,10 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) h[idx] = T(0);
             }
             __syncthreads();
-            if (pg.rhs_hs_store[ci] >= 0) {
-                T* out = d.field[pg.rhs_hs_store[ci]];
-                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                    int z = idx / nx, x = idx - z * nx;
-                    out[cell_of(z, x)] = h[idx];
-                }
-            }
-            if (!pg.rhs_dct) { __syncthreads(); continue; }
+            if (MODE == 0 && pg.rhs_hs_store[ci] >= 0) store_slab(d.field[pg.rhs_hs_store[ci]], h);
+            if (MODE == 0 && !pg.rhs_dct) { __syncthreads(); continue; }
             // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
-            if (pg.rhs_copy[ci] < 0) {
+            if (MODE != 0 || pg.rhs_copy[ci] < 0) {
                 const T* __restrict__ m1 = d.field[pg.state[0]];
                 const T* __restrict__ m2 = d.field[pg.state[1]];
                 const T* __restrict__ m3 = d.field[pg.state[2]];
@@ -245,9 +322,51 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
                 const T hea = T(F.he[a]), heal = T(F.he[a] - (double)hea);
                 const int sz = nx * ny;
+                if constexpr (kVec) {
+                    // four consecutive x cells per thread: the state, the y and z neighbour rows as
+                    // float4, the two outer x neighbours as scalars (mirror ghosts at the ends)
+                    constexpr int N4 = NX / 4;
+                    const T* r1 = m1 + cbase;
+                    const T* r2 = m2 + cbase;
+                    const T* r3 = m3 + cbase;
+                    const T* ra = ma + cbase;
+                    for (int i = threadIdx.x; i < nz * N4; i += blockDim.x) {
+                        const int z = i / N4, x4 = i - z * N4;
+                        const int o = z * zstride + 4 * x4;
+                        const float4 A1 = ld4(r1 + o), A2 = ld4(r2 + o), A3 = ld4(r3 + o);
+                        const float4 C = a == 0 ? A1 : (a == 1 ? A2 : A3);
+                        const float4 YP = y + 1 < ny ? ld4(ra + o + nx) : C;
+                        const float4 YM = y > 0 ? ld4(ra + o - nx) : C;
+                        const float4 ZP = z + 1 < nz ? ld4(ra + o + zstride) : C;
+                        const float4 ZM = z > 0 ? ld4(ra + o - zstride) : C;
+                        const float XM = x4 > 0 ? ra[o - 1] : C.x;
+                        const float XP = x4 + 1 < N4 ? ra[o + 4] : C.w;
+                        const float4 HV = ld4(h + 4 * i);
+                        const float a1[4] = {A1.x, A1.y, A1.z, A1.w}, a2[4] = {A2.x, A2.y, A2.z, A2.w};
+                        const float a3[4] = {A3.x, A3.y, A3.z, A3.w}, cc[4] = {C.x, C.y, C.z, C.w};
+                        const float yp[4] = {YP.x, YP.y, YP.z, YP.w}, ym[4] = {YM.x, YM.y, YM.z, YM.w};
+                        const float zp[4] = {ZP.x, ZP.y, ZP.z, ZP.w}, zm[4] = {ZM.x, ZM.y, ZM.z, ZM.w};
+                        const float hv[4] = {HV.x, HV.y, HV.z, HV.w};
+                        float rr[4];
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float c0 = cc[k];
+                            const float xl = k > 0 ? cc[k - 1] : XM, xr = k < 3 ? cc[k + 1] : XP;
+                            const float lap = ihx * ((xr - c0) + (xl - c0)) + ihy * ((yp[k] - c0) + (ym[k] - c0)) +
+                                              ihz * ((zp[k] - c0) + (zm[k] - c0));
+                            const float mu = a1[k] * ux + a2[k] * uy + a3[k] * uz;
+                            const float he = d.he_cell ? d.he_cell[(cbase + o + k) * 3 + a] : hea;
+                            const float hel = d.he_cell ? 0.f : heal;
+                            const float f = -Q * (c0 - mu * ua) + hv[k] + he;
+                            const float xx = f + fmaf(eph, lap, fmaf(epl, lap, hel));
+                            rr[k] = fmaf(sch, xx, scl * xx);
+                        }
+                        st4(h + 4 * i, make_float4(rr[0], rr[1], rr[2], rr[3]));
+                    }
+                }
                 // batches of kB cells per thread: every load of the batch is issued before any use
                 constexpr int kB = sizeof(T) == 4 ? 4 : 2;
-                for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
+                for (int i0 = threadIdx.x; !kVec && i0 < nxz; i0 += kB * blockDim.x) {
                     // the stencil reads the hi part of a double-float state: its neighbour differences are
                     // O(h^2 |Delta m|) and the lo parts change them below the FP32 operator rounding
                     T v1[kB], v2[kB], v3[kB], mc[kB], nb[kB][6];
@@ -318,24 +437,14 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             } else {
                 dct2_lines<T>(h, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
             }
-            {
-                T* out = d.field[pg.rhs_out[ci]];
-                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                    int z = idx / nx, x = idx - z * nx;
-                    out[cell_of(z, x)] = h[idx];
-                }
-            }
+            store_slab(d.field[pg.rhs_out[ci]], h);
             __syncthreads();
         }
 
         // ---- phase I: inverse DCT of solved spectra -> delta slabs ------------------------------
-        for (int i = 0; i < pg.n_inv; ++i) {
+        for (int i = 0; MODE != 1 && i < pg.n_inv; ++i) {
             T* s = slabs + i * S;
-            const T* in = d.field[pg.inv_in[i]];
-            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                int z = idx / nx, x = idx - z * nx;
-                s[idx] = in[cell_of(z, x)];
-            }
+            load_slab(s, d.field[pg.inv_in[i]]);
             __syncthreads();
             bool zdone = false;
             if constexpr (ZTC) {
@@ -366,17 +475,11 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 dct3_lines<T>(s, Lines{nx, 1, nx}, nz, xw0, xw1, pdz, stw);
             }
             dct3_lines<T, NX>(s, Lines{nz, nx, 1}, nx, xw0, xw1, pdx, stw);
-            if (pg.inv_store[i] >= 0) {
-                T* out = d.field[pg.inv_store[i]];
-                for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                    int z = idx / nx, x = idx - z * nx;
-                    out[cell_of(z, x)] = s[idx];
-                }
-            }
+            if (pg.inv_store[i] >= 0) store_slab(d.field[pg.inv_store[i]], s);
         }
 
         // ---- phase U: pointwise updates ----------------------------------------------------------
-        if (pg.op == 1) {
+        if ((MODE == 0 || MODE == 2) && pg.op == 1) {
             // Gauss-Seidel cross product: out = base + p*q - r*s  (delta form, see host program)
             T* out = d.field[pg.gs_out];
             T* outl = d.flo[pg.gs_out];
@@ -384,8 +487,45 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             const T* bl_ = pg.gs_base >= 0 ? d.flo[pg.gs_base] : nullptr;
             const T* ql_ = pg.gs_q >= 0 ? d.flo[pg.gs_q] : nullptr;
             const T* sl_ = pg.gs_s >= 0 ? d.flo[pg.gs_s] : nullptr;
+            if constexpr (kVec) {
+                constexpr int N4 = NX / 4;
+                const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                auto ldr = [&](int ref, int o, int i) -> float4 {
+                    return ref >= 0 ? ld4(d.field[ref] + cbase + o) : ld4(slabs + (-1 - ref) * S + 4 * i);
+                };
+                for (int i = threadIdx.x; i < nz * N4; i += blockDim.x) {
+                    const int z = i / N4, x4 = i - z * N4;
+                    const int o = z * zstride + 4 * x4;
+                    const float4 B4 = ldr(pg.gs_base, o, i), P4 = ldr(pg.gs_p, o, i), Q4 = ldr(pg.gs_q, o, i);
+                    const float4 R4 = ldr(pg.gs_r, o, i), S4 = ldr(pg.gs_s, o, i);
+                    const float4 BL4 = bl_ ? ld4(bl_ + cbase + o) : zero4, QL4 = ql_ ? ld4(ql_ + cbase + o) : zero4;
+                    const float4 SL4 = sl_ ? ld4(sl_ + cbase + o) : zero4;
+                    const float bb[4] = {B4.x, B4.y, B4.z, B4.w}, pp[4] = {P4.x, P4.y, P4.z, P4.w};
+                    const float qq[4] = {Q4.x, Q4.y, Q4.z, Q4.w}, rr[4] = {R4.x, R4.y, R4.z, R4.w};
+                    const float ss[4] = {S4.x, S4.y, S4.z, S4.w}, bl[4] = {BL4.x, BL4.y, BL4.z, BL4.w};
+                    const float ql[4] = {QL4.x, QL4.y, QL4.z, QL4.w}, sl[4] = {SL4.x, SL4.y, SL4.z, SL4.w};
+                    float oh[4], ol[4];
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (outl) {
+                            const float rs = fmaf(rr[k], sl[k], rr[k] * ss[k]);
+                            const float inc = fmaf(pp[k], qq[k], fmaf(pp[k], ql[k], -rs));
+                            float hi, e;
+                            two_sum(bb[k], inc, hi, e);
+                            fast_two_sum(hi, e + bl[k], oh[k], ol[k]);
+                        } else {
+                            oh[k] = bb[k] + (pp[k] * qq[k] - rr[k] * ss[k]);
+                            ol[k] = 0.f;
+                        }
+                    }
+                    const float4 OH = make_float4(oh[0], oh[1], oh[2], oh[3]);
+                    st4(out + cbase + o, OH);
+                    if (outl) st4(outl + cbase + o, make_float4(ol[0], ol[1], ol[2], ol[3]));
+                    st4(res + 4 * i, OH);
+                }
+            }
             constexpr int kB = sizeof(T) == 4 ? 4 : 2;
-            for (int i0 = threadIdx.x; i0 < nxz; i0 += kB * blockDim.x) {
+            for (int i0 = threadIdx.x; !kVec && i0 < nxz; i0 += kB * blockDim.x) {
                 T bb[kB], pp[kB], qq[kB], rr[kB], ss[kB], bl[kB], ql[kB], sl[kB];
     #pragma unroll
                 for (int u = 0; u < kB; ++u) {
@@ -425,62 +565,86 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 }
             }
             __syncthreads();
-        } else if (pg.op == 2) {
+        } else if ((MODE == 0 || MODE == 3) && pg.op == 2) {
             // Step 2 + Step 3: m*** = m** + delta (+ dt f_e), m^{n+1} = m*** / |m***|
             const double tnow = F.t0 + (double)(*d.step_ctr) * F.dt;
             const bool dfl = d.flo[pg.fin_out[0]] != nullptr;
-            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+            // forcing of the manufactured solution (Sec. 5.1) added to m*** in FP64
+            auto force = [&](T (&h)[3], T (&l)[3], int x, int z) {
+                double fe[3];
+                mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
+    #pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double v = (double)h[i] + (double)l[i] + F.dt * fe[i];
+                    h[i] = (T)v;
+                    l[i] = (T)(v - (double)h[i]);
+                }
+            };
+            if constexpr (kVec) {
+                // double-float state, four cells per thread
+                constexpr int N4 = NX / 4;
+                for (int i = threadIdx.x; i < nz * N4; i += blockDim.x) {
+                    const int z = i / N4, x4 = i - z * N4;
+                    const int o = z * zstride + 4 * x4;
+                    float mh[3][4], ml[3][4], dl[3][4];
+    #pragma unroll
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        const float4 a = ld4(d.field[pg.fin_in[c3]] + cbase + o);
+                        const float4 b = ld4(d.flo[pg.fin_in[c3]] + cbase + o);
+                        const float4 e = ld4(slabs + c3 * S + 4 * i);
+                        mh[c3][0] = a.x; mh[c3][1] = a.y; mh[c3][2] = a.z; mh[c3][3] = a.w;
+                        ml[c3][0] = b.x; ml[c3][1] = b.y; ml[c3][2] = b.z; ml[c3][3] = b.w;
+                        dl[c3][0] = e.x; dl[c3][1] = e.y; dl[c3][2] = e.z; dl[c3][3] = e.w;
+                    }
+                    float oh[3][4], ol[3][4], vv[3][4];
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float hh[3], ll[3], qh[3], ql[3];
+    #pragma unroll
+                        for (int c3 = 0; c3 < 3; ++c3) {
+                            float s1, e1;
+                            two_sum(mh[c3][k], dl[c3][k], s1, e1);
+                            fast_two_sum(s1, e1 + ml[c3][k], hh[c3], ll[c3]);
+                        }
+                        if (F.forcing) force(hh, ll, 4 * x4 + k, z);
+                        if (!project_df(hh, ll, qh, ql)) atomicOr(d.status, 1);
+    #pragma unroll
+                        for (int c3 = 0; c3 < 3; ++c3) {
+                            oh[c3][k] = qh[c3];
+                            ol[c3][k] = ql[c3];
+                            vv[c3][k] = hh[c3] + ll[c3];
+                        }
+                    }
+    #pragma unroll
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        const float4 O = make_float4(oh[c3][0], oh[c3][1], oh[c3][2], oh[c3][3]);
+                        st4(d.field[pg.fin_out[c3]] + cbase + o, O);
+                        st4(d.flo[pg.fin_out[c3]] + cbase + o, make_float4(ol[c3][0], ol[c3][1], ol[c3][2], ol[c3][3]));
+                        st4(slabs + c3 * S + 4 * i, O);
+                        if (pg.fin_v[c3] >= 0)
+                            st4(d.field[pg.fin_v[c3]] + cbase + o, make_float4(vv[c3][0], vv[c3][1], vv[c3][2], vv[c3][3]));
+                    }
+                }
+            }
+            for (int idx = threadIdx.x; !kVec && idx < nxz; idx += blockDim.x) {
                 int z = idx / nx, x = idx - z * nx;
                 long long c = cell_of(z, x);
                 if (dfl) {
                     // m*** = m** + delta in double-float, then |m***|^-1 by one double-float Newton step
-                    T h[3], l[3];
+                    T h[3], l[3], oh[3], ol[3];
     #pragma unroll
                     for (int i = 0; i < 3; ++i) {
                         T s1, e1;
                         two_sum(d.field[pg.fin_in[i]][c], slabs[i * S + idx], s1, e1);
                         fast_two_sum(s1, e1 + d.flo[pg.fin_in[i]][c], h[i], l[i]);
                     }
-                    if (F.forcing) {
-                        double fe[3];
-                        mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
-    #pragma unroll
-                        for (int i = 0; i < 3; ++i) {
-                            double v = (double)h[i] + (double)l[i] + F.dt * fe[i];
-                            h[i] = (T)v;
-                            l[i] = (T)(v - (double)h[i]);
-                        }
-                    }
-                    T p0, e0, p1, e1, p2, e2;
-                    two_prod(h[0], h[0], p0, e0);
-                    two_prod(h[1], h[1], p1, e1);
-                    two_prod(h[2], h[2], p2, e2);
-                    T s1, f1, n2h, f2;
-                    two_sum(p0, p1, s1, f1);
-                    two_sum(s1, p2, n2h, f2);
-                    T n2l = f1 + f2 + e0 + e1 + e2 + T(2) * (h[0] * l[0] + h[1] * l[1] + h[2] * l[2]);
-                    T nh, nl;
-                    fast_two_sum(n2h, n2l, nh, nl);
-                    if (!(nh > T(0)) || !isfinite(nh)) {
-                        atomicOr(d.status, 1);
-                        nh = T(1);
-                        nl = T(0);
-                    }
-                    const T r0 = rsqrt(nh);
-                    T q, qe, a, ae;
-                    two_prod(r0, r0, q, qe);
-                    two_prod(nh, q, a, ae);
-                    const T rho = ((T(1) - a) - ae) - (nh * qe + nl * q);
-                    const T cc = T(0.5) * r0 * rho;                  // 1/|m***| = r0 + cc
+                    if (F.forcing) force(h, l, x, z);
+                    if (!project_df(h, l, oh, ol)) atomicOr(d.status, 1);
     #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        T pp, pe;
-                        two_prod(h[i], r0, pp, pe);
-                        T oh, ol;
-                        fast_two_sum(pp, pe + (h[i] * cc + l[i] * r0), oh, ol);
-                        d.field[pg.fin_out[i]][c] = oh;
-                        d.flo[pg.fin_out[i]][c] = ol;
-                        slabs[i * S + idx] = oh;
+                        d.field[pg.fin_out[i]][c] = oh[i];
+                        d.flo[pg.fin_out[i]][c] = ol[i];
+                        slabs[i * S + idx] = oh[i];
                         if (pg.fin_v[i] >= 0) d.field[pg.fin_v[i]][c] = h[i] + l[i];
                     }
                     continue;
@@ -512,17 +676,13 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         }
 
         // ---- phase F: forward zero-padded FFT (x R2C, z C2C) -> spectral slots ---------------------
-        if (stray) {
+        if (MODE != 1 && stray) {
             for (int i = 0; i < pg.n_fwd; ++i) {
                 const int ref = pg.fwd_src[i];
                 const T* src;
                 if (ref >= 0) {
                     T* s0 = slabs;
-                    const T* in = d.field[ref];
-                    for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
-                        int z = idx / nx, x = idx - z * nx;
-                        s0[idx] = in[cell_of(z, x)];
-                    }
+                    load_slab(s0, d.field[ref]);
                     __syncthreads();
                     src = s0;
                 } else {
@@ -766,6 +926,11 @@ __global__ void __launch_bounds__(kThreads) y_stray_kernel(Dev<T> d, const int4*
     }
 }
 
+// Twiddle precision of the stray pass's y transforms: the stray field enters each step scaled by
+// dt, so the fixed rounding of FP32 twiddles there perturbs the increment far less than in the
+// heat solves; hi parts only
+constexpr bool kStrayTwLo = false;
+
 // Register-resident stray-field line pass: one warp per kx line (Py = 32 E, E in {2,4,8,16}).
 // The CTA first issues asynchronous copies of everything it reads: for each input component b
 // the (y < ny, kx0..kx0+lines) tile of the x,z spectrum (fresh components only) and the Newell
@@ -851,7 +1016,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
                 const int y = lane + 32 * k;
                 v[k] = y < ny ? line[y] : cmk<V>(T(0), T(0));
             }
-            wreg_fwd<T, E>(v, scr, stw, lane);
+            wreg_fwd<T, E, kStrayTwLo>(v, scr, stw, lane);
             if ((pg.store_mask >> b) & 1) {
 #pragma unroll
                 for (int s1 = 0; s1 < E; ++s1) cb[s1 * 32] = v[s1];
@@ -881,7 +1046,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     const long long out0 = line0 + warp;
 #pragma unroll
     for (int o = 0; o < NOUT; ++o) {
-        wreg_adj<T, E>(acc[o], scr, stw, lane);
+        wreg_adj<T, E, kStrayTwLo>(acc[o], scr, stw, lane);
         V* Ho = d.spec[pg.out_spec[o]] + out0;
 #pragma unroll
         for (int k = 0; k < E; ++k) {

@@ -181,3 +181,20 @@ def test_step_before_set_field_is_a_state_error():
         H.step(1)
     assert e.value.code == sgspm.ERR_STATE
     H.close()
+
+
+def test_fp32_batch_with_misaligned_film_matches_oracle():
+    # the compile-time slab kernels move four cells per access; a power-of-two film whose pool
+    # offset is not a multiple of four (it follows a 15-cell film) runs the runtime-length kernel
+    films = [dict(n=(32, 8, 2), h=(1 / 32,) * 3, eps=0.016, Q=0.01, alpha=0.02, dt=0.01, he=(0.02, 0, 0)),
+             dict(n=(5, 3, 1), h=(0.2,) * 3, eps=0.016, Q=0.01, alpha=0.05, dt=0.01, he=(0.0, 0.01, 0)),
+             dict(n=(16, 8, 2), h=(1 / 16,) * 3, eps=0.02, Q=0.01, alpha=0.001, dt=0.01, he=(-0.02, 0, 0))]
+    H = sgspm.Handle(films, fp64=False)
+    m0s = [inputs.random_unit(40 + i, f["n"]) for i, f in enumerate(films)]
+    H.set_m(np.concatenate([m.reshape(-1) for m in m0s]))
+    H.step(6)
+    gots = H.split(H.get_m())
+    H.close()
+    for f, m0, got in zip(films, m0s, gots):
+        ref, _ = oracle_run(m0, steps=6, **f)
+        assert np.abs(got - ref).max() <= 1e-5
