@@ -206,6 +206,20 @@ int sgspm_profile_step(sgspm_t h, float* ms, int* kind, int cap);
 int sgspm_launches_per_step(sgspm_t h);
 
 /*
+ * Test support for the bounded waits of the tensor-core (SGSPM_TF32X3) form; the paper has no
+ * counterpart.  Every slab-pass CTA of that form waits on an mbarrier for its tcgen05.mma
+ * results, with a limit of about one second (or 2^24 polls); a wait that runs out sets a status
+ * bit, skips the tensor-memory reads and frees its tensor memory, and the next synchronising
+ * call returns SGSPM_ERR_TIMEOUT.  With skip_mma != 0 the slab passes issue neither the MMAs
+ * nor their commit, so every such wait runs out with nothing in flight; wait_limit > 0
+ * replaces the poll limit (0 restores it).  The switches stay until changed; results computed
+ * while skip_mma is set are invalid, and the status stays latched on the handle.
+ * Errors: SGSPM_ERR_ARG (NULL handle, wait_limit < 0), SGSPM_ERR_STATE (handle without the
+ * tensor-core form), SGSPM_ERR_CUDA.  Synchronises the handle's stream.
+ */
+int sgspm_test_tc_timeout(sgspm_t h, int skip_mma, int wait_limit);
+
+/*
  * sgspm_energy_noalloc - the energy of sgspm_energy for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a library-usage variant.
  *
@@ -231,7 +245,9 @@ int sgspm_launches_per_step(sgspm_t h);
  * call shares that array: calls that overlap on the GPU (unordered streams) race on it and
  * must be serialised by the caller.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Errors: SGSPM_ERR_ARG for bad arguments, SGSPM_ERR_CUDA for a
+ * before any stream capture.  The address is kept for the rest of the process, so the entry
+ * point must not be used on a device after cudaDeviceReset (or any other destruction of that
+ * device's primary context) in the same process.  Errors: SGSPM_ERR_ARG for bad arguments, SGSPM_ERR_CUDA for a
  * failed CUDA call; the text is returned by sgspm_noalloc_last_error (per host thread).
  */
 int sgspm_energy_noalloc(const sgspm_grid* grid, double eps, double Q, const double easy_axis[3],
@@ -240,6 +256,15 @@ int sgspm_energy_noalloc(const sgspm_grid* grid, double eps, double Q, const dou
 
 /* Text of the last error of sgspm_energy_noalloc on the calling host thread. */
 const char* sgspm_noalloc_last_error(void);
+
+/*
+ * Diagnostic: FP64 FMA throughput of the current device in GFLOP/s (a plain kernel of
+ * independent DFMA chains, 8 CTAs of 256 threads per SM, timed with CUDA events, best of
+ * three after a warm-up).  The roofline denominator of the FP64 form's arithmetic.  Allocates
+ * and frees a small device buffer; synchronises the device's legacy default stream.
+ * Errors: SGSPM_ERR_ARG (NULL), SGSPM_ERR_OOM, SGSPM_ERR_CUDA.
+ */
+int sgspm_fp64_fma_peak(double* gflops);
 
 /* ABI version (major*100 + minor). */
 int sgspm_version(void);

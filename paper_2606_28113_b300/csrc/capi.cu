@@ -88,6 +88,7 @@ struct sgspm_ctx {
     void* d_he = nullptr;
     bool he_cell = false;
     int* d_status = nullptr;
+    int* d_tc_test = nullptr;          // tensor-core wait test switches (TF32X3 form; see sgspm_test_tc_timeout)
     long long* d_step = nullptr;
     void* d_stage = nullptr;
     // launches are split by size class: one instantiation of a pass per class of films
@@ -208,6 +209,7 @@ static Dev<T> dev_view(sgspm_ctx* ctx) {
     d.ycache_n = ctx->nycache;
     d.status = ctx->d_status;
     d.step_ctr = ctx->d_step;
+    d.tc_test = ctx->d_tc_test;
     return d;
 }
 
@@ -1365,6 +1367,10 @@ static int setup_t(sgspm_ctx* ctx) {
     }
     CK(cudaMalloc(&ctx->d_stage, (size_t)3 * ctx->ncell * sizeof(double)));
     CK(cudaMalloc(&ctx->d_status, sizeof(int)));
+    if (ctx->tf32x3) {
+        CK(cudaMalloc(&ctx->d_tc_test, 2 * sizeof(int)));
+        CK(cudaMemset(ctx->d_tc_test, 0, 2 * sizeof(int)));
+    }
     CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
     CK(cudaMalloc(&ctx->d_step, sizeof(long long)));
     CK(cudaMemset(ctx->d_step, 0, sizeof(long long)));
@@ -1390,7 +1396,7 @@ static void release(sgspm_ctx* ctx) {
     for (int i = 0; i < kMaxSpec; ++i)
         if (ctx->d_spec[i]) cudaFree(ctx->d_spec[i]);
     void* more[] = {ctx->d_tab, ctx->d_tab_lo, ctx->d_tab_spec, ctx->d_ckpt, ctx->d_seg, ctx->d_final, ctx->d_apart,
-                    ctx->d_alpha_b, ctx->d_ycache};
+                    ctx->d_alpha_b, ctx->d_ycache, ctx->d_tc_test};
     for (void* p : more)
         if (p) cudaFree(p);
     for (int n = 0; n < 4; ++n)
@@ -1630,7 +1636,7 @@ static int grad_t(sgspm_ctx* ctx, const void* dL_dmT, int dtype, void* dL_dhe, d
 
 extern "C" {
 
-int sgspm_version(void) { return 100; }
+int sgspm_version(void) { return 101; }
 
 const char* sgspm_last_error(sgspm_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
@@ -2099,6 +2105,47 @@ int sgspm_grad(sgspm_t ctx, const void* dL_dmT, int dtype, void* dL_dhe, double*
                      : grad_t<float>(ctx, dL_dmT, dtype, dL_dhe, dL_dalpha);
 }
 
+
+int sgspm_fp64_fma_peak(double* gflops) {
+    if (!gflops) return SGSPM_ERR_ARG;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SGSPM_ERR_CUDA;
+    const int blocks = nsm * 8, threads = 256, iters = 1 << 14;
+    double* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = SGSPM_OK;
+    if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) return SGSPM_ERR_OOM;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SGSPM_ERR_CUDA;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && rc == SGSPM_OK; ++rep) {
+        cudaEventRecord(e0, 0);
+        fp64_fma_probe_kernel<<<blocks, threads>>>(iters, out);
+        cudaEventRecord(e1, 0);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            rc = SGSPM_ERR_CUDA;
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;   // the first launch is a warm-up
+    }
+    if (rc == SGSPM_OK) *gflops = 2.0 * kFmaChains * (double)iters * blocks * threads / (best * 1e-3) / 1e9;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    return rc;
+}
+
+int sgspm_test_tc_timeout(sgspm_t ctx, int skip_mma, int wait_limit) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!ctx->d_tc_test) return fail(ctx, SGSPM_ERR_STATE, "the handle has no tensor-core transforms (TF32X3 form only)");
+    if (wait_limit < 0) return fail(ctx, SGSPM_ERR_ARG, "wait_limit must be >= 0");
+    const int v[2] = {skip_mma ? 1 : 0, wait_limit};
+    CK(cudaMemcpyAsync(ctx->d_tc_test, v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SGSPM_OK;
+}
 
 int sgspm_launches_per_step(sgspm_t ctx) {
     if (!ctx) return SGSPM_ERR_ARG;

@@ -193,6 +193,10 @@ struct Dev {
     long long ycache_n;
     int* status;
     const long long* step_ctr;
+    // test support of the tensor-core form: [0] != 0 skips the MMA issue and commit (so that the
+    // bounded completion wait runs out with nothing in flight), [1] > 0 replaces the wait's
+    // iteration limit; null outside that form.  Only sgspm_test_tc_timeout writes it.
+    const int* tc_test;
 };
 
 // ---- programmatic dependent launch ------------------------------------------------------------

@@ -153,3 +153,26 @@ __global__ void he_interleave_kernel(T* __restrict__ dst, const T* __restrict__ 
 __global__ void step_counter_kernel(long long* ctr) { *ctr += 1; }
 
 }  // namespace sgspm
+
+namespace sgspm {
+
+// FP64 FMA throughput probe: every thread runs kChains independent DFMA chains of `iters` steps
+// (a x + b with |a| < 1, so values stay finite) and writes their sum, so nothing is optimised
+// away.  2 * kChains * iters flops per thread.
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters, double* __restrict__ out) {
+    double v[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) v[c] = 1e-3 * (threadIdx.x + c);
+    const double a = 0.999999, b = 1e-9;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) v[c] = fma(v[c], a, b);
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += v[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace sgspm

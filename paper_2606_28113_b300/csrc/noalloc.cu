@@ -1,5 +1,5 @@
 // sgspm_energy_noalloc: the discrete-energy reduction for callers that must not allocate
-// device memory.  Compiled as part of capi.cu (single translation unit).
+// device memory.  Included by capi.cu.
 //
 // Who needs it: code that runs where cudaMalloc / cudaFree are not available or not
 // allowed - a plugin inside a host application that owns every device buffer through its
@@ -28,7 +28,8 @@ constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[4 * kNoallocMaxBlocks];
 
-// Address of g_noalloc_partials on each device, looked up once per device.
+// Address of g_noalloc_partials on each device, looked up once per device and kept for the rest
+// of the process (valid while that device's primary context lives: not across cudaDeviceReset).
 static double* g_noalloc_ptr[kNoallocMaxDevices] = {};
 static std::mutex g_noalloc_mu;
 

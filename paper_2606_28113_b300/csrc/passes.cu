@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             bool zdone = false;
             if constexpr (ZTC) {
                 if (tcz) {
-                    tc_zdct(h, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb, tcb + kTcBBytes, tcs, d.status);
+                    tc_zdct(h, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb, tcb + kTcBBytes, tcs, d.status, d.tc_test);
                     zdone = true;
                 }
             }
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             if constexpr (ZTC) {
                 if (tcz) {
                     tc_zdct(s, nx, nz, reinterpret_cast<unsigned char*>(xw0), tcb + 2 * kTcBBytes, tcb + 3 * kTcBBytes, tcs,
-                            d.status);
+                            d.status, d.tc_test);
                     zdone = true;
                 }
             }

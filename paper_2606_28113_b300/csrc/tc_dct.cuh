@@ -88,9 +88,11 @@ __device__ __forceinline__ void tc_setup(TcState& s, uint32_t* tmem_slot, uint64
     s.phase = 0;
 }
 
-// Bounded wait on the completion barrier (about a second at most); false if it expired.
-__device__ __forceinline__ bool tc_wait(TcState& s) {
+// Bounded wait on the completion barrier (about a second at most, or `limit` polls when limit > 0);
+// false if it expired.
+__device__ __forceinline__ bool tc_wait(TcState& s, int limit = 0) {
     const long long t0 = clock64();
+    const int maxit = limit > 0 ? limit : (1 << 24);
     uint32_t done = 0;
     for (int it = 0; !done; ++it) {
         asm volatile(
@@ -98,7 +100,7 @@ __device__ __forceinline__ bool tc_wait(TcState& s) {
             : "=r"(done)
             : "r"(s.mbar), "r"(s.phase)
             : "memory");
-        if (!done && (it > (1 << 24) || clock64() - t0 > 2000000000LL)) return false;
+        if (!done && (it > maxit || clock64() - t0 > 2000000000LL)) return false;
     }
     s.phase ^= 1u;
     return true;
@@ -126,9 +128,11 @@ __device__ __forceinline__ void tc_write_b(const float* C, int nz, unsigned char
 // In place: h[k][x] <- sum_z h[z][x] B[k][z] for k < nz, on the tensor cores.  abuf: 2 * (nx/128)
 // tiles of 4096 bytes (16-byte aligned) of scratch; bhi / blo from tc_write_b.  Ends with a
 // block barrier.  A wait that expires sets bit 4 of the status word (the slab is then left as
-// it was; the host reports SGSPM_ERR_TIMEOUT).
+// it was; the host reports SGSPM_ERR_TIMEOUT).  test: see Dev::tc_test (null in normal use).
 __device__ __forceinline__ void tc_zdct(float* h, int nx, int nz, unsigned char* abuf, const unsigned char* bhi,
-                                        const unsigned char* blo, TcState& s, int* status) {
+                                        const unsigned char* blo, TcState& s, int* status, const int* test) {
+    const bool skip = test && test[0] != 0;
+    const int limit = test ? test[1] : 0;
     const int ntile = nx / kTcM;
     unsigned char* ahi = abuf;
     unsigned char* alo = abuf + ntile * kTcTileBytes;
@@ -143,7 +147,7 @@ __device__ __forceinline__ void tc_zdct(float* h, int nx, int nz, unsigned char*
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> MMA reads
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !skip) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint64_t bh = tc_desc(smem_u32(bhi)), bl = tc_desc(smem_u32(blo));
         for (int t = 0; t < ntile; ++t) {
@@ -156,7 +160,7 @@ __device__ __forceinline__ void tc_zdct(float* h, int nx, int nz, unsigned char*
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s.mbar)
                      : "memory");
     }
-    const bool ok = tc_wait(s);
+    const bool ok = tc_wait(s, limit);
     if (!ok && threadIdx.x == 0) atomicOr(status, 4);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -67,6 +67,8 @@ def lib():
     L.sgspm_last_error.argtypes = [vp]
     L.sgspm_last_error.restype = ctypes.c_char_p
     L.sgspm_launches_per_step.argtypes = [vp]
+    L.sgspm_test_tc_timeout.argtypes = [vp, i, i]
+    L.sgspm_fp64_fma_peak.argtypes = [dp]
     L.sgspm_profile_step.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int), i]
     L.sgspm_version.argtypes = []
     L.sgspm_record.argtypes = [vp, ll, i]
@@ -82,6 +84,7 @@ def lib():
                  "sgspm_set_field",
                  "sgspm_get_field", "sgspm_step", "sgspm_energy", "sgspm_set_forcing", "sgspm_set_time",
                  "sgspm_get_time", "sgspm_sync", "sgspm_destroy", "sgspm_launches_per_step", "sgspm_version",
+                 "sgspm_test_tc_timeout", "sgspm_fp64_fma_peak",
                  "sgspm_profile_step"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -313,6 +316,10 @@ class Handle:
     def launches_per_step(self):
         return lib().sgspm_launches_per_step(self.h)
 
+    def test_tc_timeout(self, skip_mma, wait_limit=0):
+        """Test support (TF32X3 form): skip the tensor-core MMAs so that their bounded waits run out."""
+        self._check(lib().sgspm_test_tc_timeout(self.h, int(bool(skip_mma)), int(wait_limit)))
+
     def profile_step(self):
         """One step with per-launch device times: list of (kind, ms)."""
         cap = self.launches_per_step() + 4
@@ -381,6 +388,15 @@ def energy_noalloc(n, h, eps, Q, u, he, m, hs, out, stream=None):
                                     ctypes.c_void_p(out.data_ptr()), _stream(stream))
     if rc != OK:
         raise SGSPMError(rc, lib().sgspm_noalloc_last_error().decode())
+
+
+def fp64_fma_peak():
+    """Measured FP64 FMA throughput of the current device (GFLOP/s)."""
+    v = ctypes.c_double(0.0)
+    rc = lib().sgspm_fp64_fma_peak(ctypes.byref(v))
+    if rc < 0:
+        raise SGSPMError(rc, "sgspm_fp64_fma_peak failed")
+    return v.value
 
 
 def film(n, h, eps, Q, alpha, dt, u=(1.0, 0.0, 0.0), he=(0.0, 0.0, 0.0), **kw):

@@ -27,7 +27,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_version():
-    assert sgspm.lib().sgspm_version() == 100
+    assert sgspm.lib().sgspm_version() == 101
 
 
 def _create(grid, eps=0.1, Q=0.1, alpha=0.1, dt=0.01, u=(1.0, 0.0, 0.0)):
@@ -71,3 +71,4 @@ def test_null_handle_tuning_and_parameter_calls_are_rejected():
     assert L.sgspm_autotune(None, 1, None, 0) == sgspm.ERR_ARG
     assert L.sgspm_heat_tile(None) == sgspm.ERR_ARG
     assert L.sgspm_set_heat_tile(None, 6) == sgspm.ERR_ARG
+    assert L.sgspm_test_tc_timeout(None, 1, 0) == sgspm.ERR_ARG

@@ -8,11 +8,14 @@ with respect to the per-cell applied field h_e and the damping alpha.
     1e-8 (FD converges to the adjoint as the step shrinks; at 1e-6 it has not yet converged after
     500 steps from a random texture).  h_e along a random direction over 500 steps; alpha over
     50 steps: after 500 steps dL/dalpha is ~2e4 and FD does not converge before FP64 rounding
-    takes over, so alpha is checked there against autograd at 16x16x2 instead.  Target 1e-4 for
-    the FP64 form.  The FP32 form's own trajectory leaves the FP64 one on a random texture (the
-    rounding amplification of the forward tests), so at full size it is held to 2e-3 (direction)
-    and 5e-3 (alpha) after 50 steps and only reported after 500; its 1e-4 check is the 16x16x2
-    comparison above.
+    takes over, so alpha is checked there against autograd at 16x16x2 instead.  Target 1e-4
+    relative, for both forms after 50 steps and for the FP64 form after 500.
+  * After 500 steps from the i.i.d. random texture the trajectory itself amplifies rounding:
+    the FP64 forward started from m0 changed by FP32-sized noise (6e-8) ends as far from the
+    unperturbed one as the FP32 form does, so no FP32 computation can reproduce the FP64
+    gradient there; a test measures that amplification.  From a smooth texture (128x128x4,
+    Gaussian-smoothed random state) the FP32 form tracks the FP64 trajectory, and its
+    500-step gradient is held to 1e-4 of the FP64 central differences.
 """
 import numpy as np
 import pytest
@@ -99,15 +102,73 @@ def test_film128x128x4_against_central_differences(steps, check_alpha):
         dv = float(np.sum(g * v))
         print(f"steps={steps} fp64={fp64}: directional {dv:.9e} vs FD {fd_v:.9e}; alpha {a:.9e} vs FD {fd_a}")
         if not fp64 and steps > 50:
-            continue
-        tol = 1e-4 if fp64 else 2e-3
-        assert abs(dv - fd_v) <= tol * abs(fd_v)
+            continue        # see test_film128x128x4_random_texture_amplifies_fp32_rounding
+        assert abs(dv - fd_v) <= 1e-4 * abs(fd_v)
         if check_alpha:
-            # dL/dalpha sums the damping-solve terms of every cell and step, so in the FP32 form it
-            # inherits the trajectory's rounding amplification in full (measured 2.0e-3 relative
-            # after 50 steps with the half-length transforms); the 1e-4 target is the FP64 form's
-            tol_a = 1e-4 if fp64 else 5e-3
-            assert abs(a - fd_a) <= tol_a * abs(fd_a)
+            assert abs(a - fd_a) <= 1e-4 * abs(fd_a)
+
+
+def _final_state(n, h, kw, alpha, m0, he, steps, fp64):
+    H = sgspm.film(n, h, alpha=alpha, fp64=fp64, **kw)
+    H.set_m(m0)
+    H.set_he(he)
+    H.step(steps)
+    mT = H.split(H.get_m())[0]
+    H.close()
+    return mT
+
+
+def test_film128x128x4_random_texture_amplifies_fp32_rounding():
+    """After 500 steps from the i.i.d. random texture, FP32-sized rounding moves the FP64
+    trajectory as far as the FP32 form is from it: an FP64 run whose state is perturbed by 6e-8
+    relative noise after every step (as FP32 rounding does) ends O(1) away from the clean run, so
+    the dynamics, not the FP32 adjoint, set the FP32 gradient's distance from the FP64 one."""
+    w = inputs.WORKLOADS["film128x128x4_adjoint"]
+    n, h = w["n"], w["h"]
+    kw = dict(eps=w["eps"], Q=w["Q"], dt=w["dt"])
+    steps = 500
+    m0 = inputs.random_unit(w["seed"], n)
+    he = 0.01 * np.random.default_rng(7).normal(size=(3, n[2], n[1], n[0]))
+    ref = _final_state(n, h, kw, w["alpha"], m0, he, steps, True)
+    rng = np.random.default_rng(9)
+    H = sgspm.film(n, h, alpha=w["alpha"], fp64=True, **kw)
+    H.set_m(m0)
+    H.set_he(he)
+    for _ in range(steps):
+        H.step(1)
+        m = H.get_m()
+        H.set_m(m * (1 + 6e-8 * rng.choice([-1, 1], size=m.shape)))
+    noisy = H.split(H.get_m())[0]
+    H.close()
+    d_noise = np.abs(noisy - ref).max()
+    d_fp32 = np.abs(_final_state(n, h, kw, w["alpha"], m0, he, steps, False) - ref).max()
+    print(f"{steps} steps, random texture: FP64 with 6e-8 noise every step vs clean {d_noise:.3e}; "
+          f"FP32 form vs FP64 {d_fp32:.3e}")
+    assert d_noise > 0.1                   # O(1) divergence from FP32-sized per-step noise ...
+    assert d_fp32 < 10 * d_noise           # ... of the same order as the FP32 form's
+
+
+def test_film128x128x4_smooth_texture_fp32_gradient_after_500_steps():
+    w = inputs.WORKLOADS["film128x128x4_adjoint"]
+    n, h = w["n"], w["h"]
+    kw = dict(eps=w["eps"], Q=w["Q"], dt=w["dt"])
+    alpha = w["alpha"]
+    m0 = inputs.smoothed_random_unit(w["seed"], n, sigma_cells=(10.0, 10.0, 10.0))
+    he = 0.01 * np.random.default_rng(7).normal(size=(3, n[2], n[1], n[0]))
+    steps, K = 500, 50
+
+    def loss64(he_):
+        mT = _final_state(n, h, kw, alpha, m0, he_, steps, True)
+        return np.mean((mT[0] - 1.0) ** 2) + REG * np.sum(he_ * he_)
+
+    v = np.random.default_rng(8).normal(size=he.shape)
+    step = 1e-8
+    fd_v = (loss64(he + step * v) - loss64(he - step * v)) / (2 * step)
+    for fp64 in (True, False):
+        L, g, a = gpu_grad(n, h, kw, alpha, m0, he, steps, K, fp64)
+        dv = float(np.sum(g * v))
+        print(f"smooth texture, {steps} steps, fp64={fp64}: directional {dv:.9e} vs FD {fd_v:.9e}")
+        assert abs(dv - fd_v) <= 1e-4 * abs(fd_v)
 
 
 def test_autograd_function_matches_torch_reference():

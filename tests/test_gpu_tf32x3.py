@@ -79,3 +79,34 @@ def test_tf32x3_strip_short_run_matches_oracle():
     ref, _ = oracle_run(m0, steps=5, **{k: W[k] for k in ("n", "h", "eps", "Q", "alpha", "dt", "u", "he")})
     got = run(m0, 5, W, tf32x3=True)
     assert np.abs(got - ref).max() <= 1e-5
+
+
+def test_tf32x3_expired_tensor_core_wait_is_reported():
+    """Failure detection without a fault: with the test switch set, the slab passes issue no MMA
+    and no commit, so every bounded mbarrier wait runs out with nothing in flight; the handle
+    then reports SGSPM_ERR_TIMEOUT at the next synchronising call, and the device stays usable."""
+    f = dict(BASE, n=(128, 8, 4), h=(1 / 128,) * 3)
+    m0 = inputs.random_unit(33, f["n"])
+    H = sgspm.film(f["n"], f["h"], f["eps"], f["Q"], f["alpha"], f["dt"], he=f["he"], tf32x3=True)
+    H.set_m(m0)
+    H.step(1)
+    H.sync()
+    H.test_tc_timeout(True, wait_limit=1000)
+    H.step(1)
+    with pytest.raises(sgspm.SGSPMError) as e:
+        H.sync()
+    assert e.value.code == sgspm.ERR_TIMEOUT
+    H.test_tc_timeout(False)
+    H.close()
+    # a fresh handle on the same device computes correct results
+    ref, _ = oracle_run(m0, steps=3, **{k: f[k] for k in ("n", "h", "eps", "Q", "alpha", "dt", "he")})
+    assert np.abs(run(m0, 3, f, tf32x3=True) - ref).max() <= 1e-5
+
+
+def test_tc_timeout_switch_needs_the_tensor_core_form():
+    f = dict(BASE, n=(16, 8, 2), h=(1 / 16,) * 3)
+    H = sgspm.film(f["n"], f["h"], f["eps"], f["Q"], f["alpha"], f["dt"], he=f["he"])
+    with pytest.raises(sgspm.SGSPMError) as e:
+        H.test_tc_timeout(True)
+    assert e.value.code == sgspm.ERR_STATE
+    H.close()
