@@ -14,6 +14,9 @@ heat     Implicit heat solve (I - c dt Delta_h)^{-1} by DCT-II/III, the mirror-g
          7-point Laplacian, and a dense LU solve of the assembled matrix.
 scheme   Effective field, the SGSPM step (Sec. 3.2), the GSPM step (Sec. 3.1), the
          discrete energy and the manufactured solutions of Sec. 5.1.
+spectral Spectral radii of the GS and SGS iteration matrices of a step (Sec. 4), from the
+         intermediates of an oracle step (block reading stated there; parity with Tables 1-2
+         unpinned).
 
 Everything is float64 numpy/scipy; every function cites the passage it follows.
 """
