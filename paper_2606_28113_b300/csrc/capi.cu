@@ -1335,6 +1335,7 @@ static int setup_t(sgspm_ctx* ctx) {
     if (ctx->dtab_host.empty()) ctx->dtab_host.push_back(0.0);
     if ((rc = upload_vec<T>(ctx, &ctx->d_dtab, ctx->dtab_host))) return rc;
     CK(cudaMalloc(&ctx->d_films, ctx->films.size() * sizeof(Film)));
+    for (Film& F : ctx->films) film_consts(F);
     CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_plans, ctx->plans.size() * sizeof(Plan)));
     CK(cudaMemcpy(ctx->d_plans, ctx->plans.data(), ctx->plans.size() * sizeof(Plan), cudaMemcpyHostToDevice));
@@ -1727,6 +1728,7 @@ int sgspm_set_applied_field(sgspm_t ctx, const double* he) {
         }
     ctx->he_cell = false;
     CK(cudaStreamSynchronize(ctx->stream));
+    for (Film& F : ctx->films) film_consts(F);
     CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
     drop_graph(ctx);
     return SGSPM_OK;
@@ -1738,6 +1740,7 @@ int sgspm_set_alpha(sgspm_t ctx, const double* alpha) {
         if (!(std::isfinite(alpha[f]) && alpha[f] >= 0)) return fail(ctx, SGSPM_ERR_ARG, "alpha must be finite and >= 0");
     for (int f = 0; f < ctx->nfilm; ++f) ctx->films[f].alpha = alpha[f];
     CK(cudaStreamSynchronize(ctx->stream));
+    for (Film& F : ctx->films) film_consts(F);
     CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
     return SGSPM_OK;
 }
@@ -1981,6 +1984,7 @@ int sgspm_set_forcing(sgspm_t ctx, int kind) {
     CK(cudaStreamSynchronize(ctx->stream));
     for (Film& F : ctx->films) F.forcing = kind;
     ctx->forcing = kind != SGSPM_FORCE_NONE;
+    for (Film& F : ctx->films) film_consts(F);
     CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
     build_programs(ctx);
     drop_graph(ctx);
@@ -1993,6 +1997,7 @@ int sgspm_set_time(sgspm_t ctx, double t) {
     CK(cudaStreamSynchronize(ctx->stream));
     for (Film& F : ctx->films) F.t0 = t;
     ctx->steps = 0;
+    for (Film& F : ctx->films) film_consts(F);
     CK(cudaMemcpy(ctx->d_films, ctx->films.data(), ctx->films.size() * sizeof(Film), cudaMemcpyHostToDevice));
     CK(cudaMemset(ctx->d_step, 0, sizeof(long long)));
     return SGSPM_OK;

@@ -121,7 +121,38 @@ struct Film {
     double u[3];
     double he[3];
     double t0;               // time at step counter 0
+    // The same parameters for the FP32 form, split hi + lo (lo = fl(v - hi)) where the kernels
+    // need the full double value, set on the host (film_consts) whenever a parameter changes:
+    // the pass kernels then run no FP64 arithmetic, which is slow on this GPU.
+    float fs_dt[2][2];       // [damp][hi, lo]: dt (Step 1), alpha dt (Step 2)
+    float fs_c[2][2];        // [damp][hi, lo]: eps dt, alpha eps dt (heat-solve coefficient)
+    float fs_eps[2];         // eps: hi, lo
+    float fs_he[3][2];       // uniform applied field: hi, lo
+    float fs_n[2];           // 1 / (nx ny nz): hi, lo
+    float fs_Q;              // Q
+    float fs_u[3];           // easy axis
+    float fs_ih[3];          // 1 / h_a^2
 };
+
+// Fill the FP32 parameter fields of a film from its FP64 parameters (host).
+inline void film_consts(Film& F) {
+    auto split = [](double v, float* o) {
+        o[0] = (float)v;
+        o[1] = (float)(v - (double)o[0]);
+    };
+    split(F.dt, F.fs_dt[0]);
+    split(F.alpha * F.dt, F.fs_dt[1]);
+    split(F.eps * F.dt, F.fs_c[0]);
+    split(F.alpha * F.eps * F.dt, F.fs_c[1]);
+    split(F.eps, F.fs_eps);
+    for (int a = 0; a < 3; ++a) split(F.he[a], F.fs_he[a]);
+    split(1.0 / ((double)F.nx * F.ny * F.nz), F.fs_n);
+    F.fs_Q = (float)F.Q;
+    for (int a = 0; a < 3; ++a) F.fs_u[a] = (float)F.u[a];
+    F.fs_ih[0] = (float)(1.0 / (F.hx * F.hx));
+    F.fs_ih[1] = (float)(1.0 / (F.hy * F.hy));
+    F.fs_ih[2] = (float)(1.0 / (F.hz * F.hz));
+}
 
 // Operand reference of a pointwise update: >= 0 real field slot, < 0 shared-memory slab (-1 - idx).
 constexpr int kMaxSlots = 64;
@@ -219,6 +250,21 @@ __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
     static_assert(BYTES == 8 || BYTES == 16, "cp.async piece of 8 or 16 bytes");
     if constexpr (BYTES == 8) cp_async_8(sdst, gsrc);
     else cp_async_16(sdst, gsrc);
+}
+__device__ __forceinline__ void cp_async_4(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+}
+// The whole CTA copies n elements of 4, 8 or 16 bytes from global to shared memory with
+// asynchronous copies (all in flight together; the caller commits and waits)
+template <typename E>
+__device__ __forceinline__ void stage_async(E* sdst, const E* gsrc, int n) {
+    static_assert(sizeof(E) == 4 || sizeof(E) == 8 || sizeof(E) == 16, "element of 4, 8 or 16 bytes");
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if constexpr (sizeof(E) == 16) cp_async_16(sdst + i, gsrc + i);
+        else if constexpr (sizeof(E) == 8) cp_async_8(sdst + i, gsrc + i);
+        else cp_async_4(sdst + i, gsrc + i);
+    }
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // wait until at most `pending` (0, 1 or 2) of this thread's committed groups are still in flight

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         const int lens[6] = {nx, nx, nz, nz, stray ? Px : 0, stray ? Pz : 0};
         int off = 0;
         for (int k = 0; k < 6; ++k) {
-            for (int i = threadIdx.x; i < lens[k]; i += blockDim.x) stw[off + i] = d.tw[segs[k] + i];
+            stage_async(stw + off, d.tw + segs[k], lens[k]);
             off += lens[k];
         }
     }
@@ -162,8 +162,9 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     V* zw1 = zw0 + Lo.zw;
     T* slabs = reinterpret_cast<T*>(zw1 + Lo.zw);
     T* sdt = slabs + 3 * Lo.slab;
-    if (Lo.dt)
-        for (int i = threadIdx.x; i < 2 * nz * nz; i += blockDim.x) sdt[i] = d.dtab[F.gdtab_z + i];
+    if (Lo.dt) stage_async(sdt, d.dtab + F.gdtab_z, 2 * nz * nz);
+    cp_async_commit();
+    cp_async_wait(0);
     __syncthreads();
     // TF32X3 form: B operands (forward hi, lo; inverse hi, lo) after the DCT tables, tensor memory
     const bool tcz = ZTC && tc_zdct_ok(nx, nz);
@@ -314,13 +315,40 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
                 // dt (alpha dt), eps and the uniform applied field are split hi + lo in the FP32
                 // form: they set the precession rate in every step, so their FP32 rounding would
                 // act as a fixed perturbation of the parameters (lo parts are zero in FP64)
-                const double sd = pg.damp ? F.alpha * F.dt : F.dt;
-                const T sch = T(sd), scl = T(sd - (double)sch);
-                const T eph = T(F.eps), epl = T(F.eps - (double)eph), Q = T(F.Q);
-                const T ux = T(F.u[0]), uy = T(F.u[1]), uz = T(F.u[2]);
-                const T ua = T(F.u[a]);
-                const T ihx = T(1.0 / (F.hx * F.hx)), ihy = T(1.0 / (F.hy * F.hy)), ihz = T(1.0 / (F.hz * F.hz));
-                const T hea = T(F.he[a]), heal = T(F.he[a] - (double)hea);
+                T sch, scl, eph, epl, Q, ux, uy, uz, ua, ihx, ihy, ihz, hea, heal;
+                if constexpr (sizeof(T) == 4) {
+                    // precomputed on the host: no FP64 arithmetic in the FP32 kernels
+                    const int dm = pg.damp ? 1 : 0;
+                    sch = F.fs_dt[dm][0];
+                    scl = F.fs_dt[dm][1];
+                    eph = F.fs_eps[0];
+                    epl = F.fs_eps[1];
+                    Q = F.fs_Q;
+                    ux = F.fs_u[0];
+                    uy = F.fs_u[1];
+                    uz = F.fs_u[2];
+                    ua = F.fs_u[a];
+                    ihx = F.fs_ih[0];
+                    ihy = F.fs_ih[1];
+                    ihz = F.fs_ih[2];
+                    hea = F.fs_he[a][0];
+                    heal = F.fs_he[a][1];
+                } else {
+                    sch = pg.damp ? F.alpha * F.dt : F.dt;
+                    scl = T(0);
+                    eph = F.eps;
+                    epl = T(0);
+                    Q = F.Q;
+                    ux = F.u[0];
+                    uy = F.u[1];
+                    uz = F.u[2];
+                    ua = F.u[a];
+                    ihx = 1.0 / (F.hx * F.hx);
+                    ihy = 1.0 / (F.hy * F.hy);
+                    ihz = 1.0 / (F.hz * F.hz);
+                    hea = F.he[a];
+                    heal = T(0);
+                }
                 const int sz = nx * ny;
                 if constexpr (kVec) {
                     // four consecutive x cells per thread: the state, the y and z neighbour rows as
@@ -567,10 +595,10 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             __syncthreads();
         } else if ((MODE == 0 || MODE == 3) && pg.op == 2) {
             // Step 2 + Step 3: m*** = m** + delta (+ dt f_e), m^{n+1} = m*** / |m***|
-            const double tnow = F.t0 + (double)(*d.step_ctr) * F.dt;
             const bool dfl = d.flo[pg.fin_out[0]] != nullptr;
             // forcing of the manufactured solution (Sec. 5.1) added to m*** in FP64
             auto force = [&](T (&h)[3], T (&l)[3], int x, int z) {
+                const double tnow = F.t0 + (double)(*d.step_ctr) * F.dt;
                 double fe[3];
                 mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
     #pragma unroll
@@ -653,6 +681,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     #pragma unroll
                 for (int i = 0; i < 3; ++i) v[i] = d.field[pg.fin_in[i]][c] + slabs[i * S + idx];
                 if (F.forcing) {
+                    const double tnow = F.t0 + (double)(*d.step_ctr) * F.dt;
                     double fe[3];
                     mms_forcing(F.forcing, (x + 0.5) * F.hx, (y + 0.5) * F.hy, (z + 0.5) * F.hz, tnow, F.alpha, fe);
     #pragma unroll
@@ -763,17 +792,17 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
     __shared__ Plan pdy;
     if (threadIdx.x == 0) pdy = d.plans[F.splan_dy];   // staged copy: twiddles at 0, quarter-wave at ny
     tw_t<T>* stw = reinterpret_cast<tw_t<T>*>(smem_raw);
-    for (int i = threadIdx.x; i < ny; i += blockDim.x) {
-        stw[i] = d.tw[F.gtw_dy + i];
-        stw[ny + i] = d.tw[F.gtw4_dy + i];
-    }
-    __syncthreads();
-    pdl_wait();
     const int npair = (tn + 1) / 2;
     V* c0 = reinterpret_cast<V*>(stw + 2 * ny);
     V* c1 = c0 + npair * ny;
     T* R = reinterpret_cast<T*>(c1 + npair * ny);
     const int LR = ny + 8;   // padded line stride: tile copies hit distinct banks
+    stage_async(stw, d.tw + F.gtw_dy, ny);
+    stage_async(stw + ny, d.tw + F.gtw4_dy, ny);
+    cp_async_commit();
+    cp_async_wait(0);
+    __syncthreads();
+    pdl_wait();
     // tile copies: thread -> column t_ld of rows y_ld, y_ld + rpp, ... (no per-element division)
     const int rpp = (int)blockDim.x / tn;
     const int t_ld = (int)threadIdx.x % tn, y_ld = (int)threadIdx.x / tn;
@@ -781,9 +810,19 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
     // eigen-scale 1 / (N (1 + c (lx + ly + lz))), c = eps dt (alpha eps dt for Step 2); in the
     // FP32 form c, 1/N and the eigenvalues are double-float so that the scale, which is applied
     // to every mode in every solve, carries no fixed table rounding
-    const double cd = (pg.damp ? F.alpha * F.eps : F.eps) * F.dt;
-    const double nd = 1.0 / ((double)nx * ny * nz);
-    const T ch = T(cd), cl = T(cd - (double)ch), nh = T(nd), nl = T(nd - (double)nh);
+    T ch, cl, nh, nl;
+    if constexpr (sizeof(T) == 4) {
+        // precomputed on the host: no FP64 arithmetic in the FP32 kernels
+        const int dm = pg.damp ? 1 : 0;
+        ch = F.fs_c[dm][0];
+        cl = F.fs_c[dm][1];
+        nh = F.fs_n[0];
+        nl = F.fs_n[1];
+    } else {
+        ch = (pg.damp ? F.alpha * F.eps : F.eps) * F.dt;
+        nh = 1.0 / ((double)nx * ny * nz);
+        cl = nl = T(0);
+    }
     const T* lx = d.lam + F.lam;
     const T* ly = lx + nx;
     const T lzh = ly[ny + kz];
@@ -959,10 +998,9 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     V* scr0 = reinterpret_cast<V*>(stw + P);
     V* inb = scr0 + kWarpLines * P;                                       // [3][lines][LI]
     T* kbuf = reinterpret_cast<T*>(inb + 3 * kWarpLines * LI);            // [3 NOUT][lines][HyP]
-    {
-        const tw_t<T>* g = d.tw + d.plans[F.plan_py].tw;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = g[i];
-    }
+    stage_async(stw, d.tw + d.plans[F.plan_py].tw, P);
+    cp_async_commit();
+    cp_async_wait(0);
     pdl_wait();
     // ---- asynchronous staging: group b = input component b and the table lines of (o, b)
     const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx0;
