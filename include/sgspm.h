@@ -71,9 +71,12 @@ enum {
     SGSPM_NO_STRAY = 1 << 2,      /* h_s = 0                                                 */
     SGSPM_FROZEN_STRAY = 1 << 3,  /* h_s(m^n) for Step 1 and h_s(m**) for Step 2             */
     SGSPM_NO_GRAPH = 1 << 4,      /* launch kernels directly instead of a captured CUDA graph */
-    SGSPM_TF32X3 = 1 << 5         /* FP32 form: short-axis (z) DCTs as 3xTF32 GEMMs on the tensor
+    SGSPM_TF32X3 = 1 << 5,        /* FP32 form: short-axis (z) DCTs as 3xTF32 GEMMs on the tensor
                                      cores (films with nx in {128, 256, 512}, 2 <= nz <= 8; other
                                      films keep the FP32 path).  Ignored with SGSPM_FP64.  */
+    SGSPM_PERSISTENT = 1 << 6     /* each step is one persistent launch over all films (see
+                                     sgspm_create_batch); FP32 form, ny <= 128 with the stray field,
+                                     no manufactured forcing; otherwise ERR_UNSUPPORTED at create */
 };
 
 /* field selectors */
@@ -218,6 +221,20 @@ int sgspm_launches_per_step(sgspm_t h);
  * tensor-core form), SGSPM_ERR_CUDA.  Synchronises the handle's stream.
  */
 int sgspm_test_tc_timeout(sgspm_t h, int skip_mma, int wait_limit);
+
+/*
+ * Test support for the bounded waits of the persistent step (SGSPM_PERSISTENT); the paper has no
+ * counterpart.  In that step a work item waits, spinning on its film's completion counter, until
+ * the film's items of the previous passes are complete; the wait is limited to wait_limit clock
+ * cycles (default 4e9, about two seconds).  A wait that runs out sets a status bit and an abandon
+ * flag that ends the launch on every CTA; the next synchronising call returns SGSPM_ERR_TIMEOUT.
+ * withhold >= 0 names one work item (a ticket of the step's queue, 0-based) that is skipped and
+ * never reported complete, so that the waits behind it run out; -1 runs every item.  The settings
+ * stay until changed; results of a step with a withheld item are invalid, and the status stays
+ * latched on the handle.  Errors: SGSPM_ERR_ARG (NULL handle, wait_limit <= 0), SGSPM_ERR_STATE
+ * (handle without SGSPM_PERSISTENT), SGSPM_ERR_CUDA.  Synchronises the handle's stream.
+ */
+int sgspm_test_persist_wait(sgspm_t h, int withhold, long long wait_limit);
 
 /*
  * sgspm_energy_noalloc - the energy of sgspm_energy for callers that cannot allocate device

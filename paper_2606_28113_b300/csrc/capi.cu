@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -122,6 +123,16 @@ struct sgspm_ctx {
     double* d_eout = nullptr;
     std::vector<Launch> step_prog, hs_prog, fwd_prog;
     std::vector<double> dtab_host;     // dense short-axis DCT tables, built with the plans
+    // persistent ensemble step (SGSPM_PERSISTENT)
+    bool persist = false;
+    PPhase* d_pph = nullptr;
+    PItem* d_pit = nullptr;
+    int* d_pfi = nullptr;
+    unsigned* d_pctl = nullptr;        // ticket, abandon flag, per-film completed items
+    int p_nphase = 0, p_items = 0, p_grid = 0;
+    size_t p_smem = 0;
+    long long p_wait_limit = 4000000000LL;   // clock cycles (about 2 s at 2 GHz)
+    int p_withhold = -1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool have_m = false;
@@ -945,10 +956,150 @@ static int drop_graph(sgspm_ctx* ctx) {
     return SGSPM_OK;
 }
 
+template <typename T>
+static size_t heat_smem(int ny, int tx);
+
+// ---- persistent ensemble step -------------------------------------------------------------------
+// Whether every film of the handle can run in the persistent kernel: FP32 form, register stray
+// pass with padded y lengths 64..256 (E = 2, 4, 8), no manufactured forcing.
+static bool persist_ok(const sgspm_ctx* ctx, std::string* why) {
+    if (ctx->fp64 || ctx->tf32x3) {
+        *why = "the persistent step runs the FP32 form only (not FP64, not TF32X3)";
+        return false;
+    }
+    if (ctx->stray && !ctx->warp_stray) {
+        *why = "the persistent step needs the register stray pass (padded y lengths 64..512)";
+        return false;
+    }
+    for (const Film& F : ctx->films)
+        if (ctx->stray && F.Py > 256) {
+            *why = "the persistent step supports films with ny <= 128 (padded y length <= 256)";
+            return false;
+        }
+    return true;
+}
+
+// Item tables of one step from the step program: phases in program order, films in order within a
+// phase, the work items of each film as the per-pass launches cut them (slab rows packed as the
+// class's packing says, heat tiles of tx_h lines, stray groups of kPersistLines lines).
+static int build_persist(sgspm_ctx* ctx) {
+    std::vector<PPhase> ph;
+    std::vector<PItem> items;
+    std::vector<int> per_film(ctx->nfilm, 0);
+    size_t smem = 0;
+    std::map<int, int> rows_of;   // slab class key -> rows per item
+    for (const auto& c : ctx->xz_cls) rows_of[c.key] = c.rows;
+    for (const Launch& L : ctx->step_prog) {
+        if (L.kind > 2) return fail(ctx, SGSPM_ERR_UNSUPPORTED, "the persistent step has no manufactured forcing");
+        PPhase P;
+        memset(&P, 0, sizeof(P));
+        P.kind = L.kind;
+        P.first = (int)items.size();
+        P.xz = L.xz;
+        P.y = L.y;
+        // films grouped by size class within the phase, so that CTAs run one class's code for long
+        // stretches (an item depends only on its own film's earlier phases)
+        std::vector<std::pair<int, int>> order;   // (class key, film)
+        for (int f = 0; f < ctx->nfilm; ++f) {
+            const Film& F = ctx->films[f];
+            const int key = L.kind == 0 ? xz_key(false, F) : L.kind == 1 ? pow2_key(F.ny, 8, 512) : F.Py;
+            order.push_back({key, f});
+        }
+        std::stable_sort(order.begin(), order.end(), [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+        for (const auto& kf : order) {
+            const int f = kf.second;
+            const Film& F = ctx->films[f];
+            auto add = [&](int4 wi, int key) {
+                PItem it;
+                memset(&it, 0, sizeof(it));
+                it.wi = wi;
+                it.key = key;
+                it.target = per_film[f];
+                it.phase = (int)ph.size();
+                items.push_back(it);
+            };
+            int nf = 0;
+            if (L.kind == 0) {
+                const int key = xz_key(false, F);
+                const int pkey = (key == 64 || key == 128 || key == 256) ? key : 0;
+                const int rows = rows_of.count(key) ? rows_of[key] : 1;
+                for (int y = 0; y < F.ny; y += rows, ++nf) add(make_int4(f, y, std::min(rows, F.ny - y), 0), pkey);
+                smem = std::max(smem, xz_smem_bytes<float>(xz_layout(F.nx, F.nz, F.Px, F.Pz, F.Kx, ctx->stray, false)));
+            } else if (L.kind == 1) {
+                const int key = pow2_key(F.ny, 8, 512);
+                const int pkey = (key == 64 || key == 128 || key == 256) ? key : 0;
+                // about 2048 cells per item (at least the tuned tile): short lines get wide tiles,
+                // since the persistent kernel keeps only two CTAs per multiprocessor
+                const int tx = std::max(ctx->tx_h, std::min(32, std::max(1, 2048 / F.ny)));
+                for (int kz = 0; kz < F.nz; ++kz)
+                    for (int x0 = 0; x0 < F.nx; x0 += tx, ++nf) add(make_int4(f, kz, x0, std::min(tx, F.nx - x0)), pkey);
+                smem = std::max(smem, heat_smem<float>(F.ny, tx));
+            } else {
+                for (int kz = 0; kz < F.Pz; ++kz)
+                    for (int x0 = 0; x0 < F.Kx; x0 += kPersistLines, ++nf)
+                        add(make_int4(f, kz, x0, std::min(kPersistLines, F.Kx - x0)), F.Py / 32);
+                smem = std::max(smem, yw_smem_bytes<float>(F.Py, L.y.n, kPersistLines));
+            }
+            per_film[f] += nf;
+        }
+        P.n = (int)items.size() - P.first;
+        ph.push_back(P);
+    }
+    if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+    for (void* p : {(void*)ctx->d_pph, (void*)ctx->d_pit, (void*)ctx->d_pfi, (void*)ctx->d_pctl})
+        if (p) cudaFree(p);
+    ctx->d_pph = nullptr;
+    ctx->d_pit = nullptr;
+    ctx->d_pfi = nullptr;
+    ctx->d_pctl = nullptr;
+    CK(cudaMalloc(&ctx->d_pph, ph.size() * sizeof(PPhase)));
+    CK(cudaMemcpy(ctx->d_pph, ph.data(), ph.size() * sizeof(PPhase), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_pit, std::max<size_t>(1, items.size()) * sizeof(PItem)));
+    CK(cudaMemcpy(ctx->d_pit, items.data(), items.size() * sizeof(PItem), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_pfi, per_film.size() * sizeof(int)));
+    CK(cudaMemcpy(ctx->d_pfi, per_film.data(), per_film.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_pctl, (2 + ctx->nfilm) * sizeof(unsigned)));
+    CK(persist_attr(smem));
+    const int per_sm = persist_blocks_per_sm(smem);
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return fail(ctx, SGSPM_ERR_UNSUPPORTED, "the persistent step does not fit on a multiprocessor");
+    ctx->p_nphase = (int)ph.size();
+    ctx->p_items = (int)items.size();
+    ctx->p_smem = smem;
+    ctx->p_grid = per_sm * nsm;
+    return SGSPM_OK;
+}
+
+// One step: reset the ticket, the abandon flag and the film counters, then the persistent launch.
+static int enqueue_persist(sgspm_ctx* ctx, cudaStream_t st) {
+    CK(cudaMemsetAsync(ctx->d_pctl, 0, (2 + ctx->nfilm) * sizeof(unsigned), st));
+    PersistArgs a;
+    a.phases = ctx->d_pph;
+    a.items = ctx->d_pit;
+    a.film_items = ctx->d_pfi;
+    a.ctl = ctx->d_pctl;
+    a.nphase = ctx->p_nphase;
+    a.items_per_step = ctx->p_items;
+    a.nsteps = 1;
+    a.stray = ctx->stray ? 1 : 0;
+    a.wait_limit = ctx->p_wait_limit;
+    a.withhold = ctx->p_withhold;
+    persist_go((unsigned)ctx->p_grid, ctx->p_smem, st, dev_view<float>(ctx), a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+    return SGSPM_OK;
+}
+
 static int capture_step(sgspm_ctx* ctx) {
     drop_graph(ctx);
+    if (ctx->persist) {
+        int rc = build_persist(ctx);
+        if (rc) return rc;
+    }
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    int rc = run_prog(ctx, ctx->step_prog, ctx->cap);
+    int rc = ctx->persist ? enqueue_persist(ctx, ctx->cap) : run_prog(ctx, ctx->step_prog, ctx->cap);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
     if (rc) {
@@ -1397,7 +1548,7 @@ static void release(sgspm_ctx* ctx) {
     for (int i = 0; i < kMaxSpec; ++i)
         if (ctx->d_spec[i]) cudaFree(ctx->d_spec[i]);
     void* more[] = {ctx->d_tab, ctx->d_tab_lo, ctx->d_tab_spec, ctx->d_ckpt, ctx->d_seg, ctx->d_final, ctx->d_apart,
-                    ctx->d_alpha_b, ctx->d_ycache, ctx->d_tc_test};
+                    ctx->d_alpha_b, ctx->d_ycache, ctx->d_tc_test, ctx->d_pph, ctx->d_pit, ctx->d_pfi, ctx->d_pctl};
     for (void* p : more)
         if (p) cudaFree(p);
     for (int n = 0; n < 4; ++n)
@@ -1415,6 +1566,7 @@ static int check_status(sgspm_ctx* ctx) {
     if (st & 1) return fail(ctx, SGSPM_ERR_NONFINITE, "non-finite value or zero vector before projection");
     if (st & 2) return fail(ctx, SGSPM_ERR_NONFINITE, "set_field: zero-length or non-finite magnetisation vector");
     if (st & 4) return fail(ctx, SGSPM_ERR_TIMEOUT, "a tensor-core transform of the slab pass did not complete in time");
+    if (st & 8) return fail(ctx, SGSPM_ERR_TIMEOUT, "a work item of the persistent step waited too long for its film's previous pass");
     return SGSPM_OK;
 }
 
@@ -1691,6 +1843,11 @@ int sgspm_create_batch(int nfilm, const sgspm_grid* grids, const double* eps, co
         ctx->films.push_back(F);
     }
     int rc = ctx->fp64 ? setup_t<double>(ctx) : setup_t<float>(ctx);
+    if (rc == SGSPM_OK && (flags & SGSPM_PERSISTENT)) {
+        std::string why;
+        if (persist_ok(ctx, &why)) ctx->persist = true;
+        else rc = fail(ctx, SGSPM_ERR_UNSUPPORTED, why);
+    }
     if (rc) {
         g_create_err = ctx->err;
         release(ctx);
@@ -1767,8 +1924,12 @@ int sgspm_step(sgspm_t ctx, long long n) {
     if (n < 1) return fail(ctx, SGSPM_ERR_ARG, "n must be >= 1");
     if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
     if (ctx->flags & SGSPM_NO_GRAPH) {
+        if (ctx->persist && !ctx->d_pctl) {
+            int rc = build_persist(ctx);
+            if (rc) return rc;
+        }
         for (long long i = 0; i < n; ++i) {
-            int rc = run_prog(ctx, ctx->step_prog, ctx->stream);
+            int rc = ctx->persist ? enqueue_persist(ctx, ctx->stream) : run_prog(ctx, ctx->step_prog, ctx->stream);
             if (rc) return rc;
         }
     } else {
@@ -1981,6 +2142,8 @@ int sgspm_set_forcing(sgspm_t ctx, int kind) {
     if (!ctx) return SGSPM_ERR_ARG;
     if (kind != SGSPM_FORCE_NONE && kind != SGSPM_FORCE_MMS_1D && kind != SGSPM_FORCE_MMS_3D)
         return fail(ctx, SGSPM_ERR_ARG, "unknown forcing kind");
+    if (ctx->persist && kind != SGSPM_FORCE_NONE)
+        return fail(ctx, SGSPM_ERR_UNSUPPORTED, "the persistent step has no manufactured forcing");
     CK(cudaStreamSynchronize(ctx->stream));
     for (Film& F : ctx->films) F.forcing = kind;
     ctx->forcing = kind != SGSPM_FORCE_NONE;
@@ -2154,7 +2317,18 @@ int sgspm_test_tc_timeout(sgspm_t ctx, int skip_mma, int wait_limit) {
 
 int sgspm_launches_per_step(sgspm_t ctx) {
     if (!ctx) return SGSPM_ERR_ARG;
-    return (int)ctx->step_prog.size();
+    return ctx->persist ? 1 : (int)ctx->step_prog.size();
+}
+
+int sgspm_test_persist_wait(sgspm_t ctx, int withhold, long long wait_limit) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!ctx->persist) return fail(ctx, SGSPM_ERR_STATE, "the handle was not created with SGSPM_PERSISTENT");
+    if (wait_limit <= 0) return fail(ctx, SGSPM_ERR_ARG, "wait_limit must be > 0");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->p_withhold = withhold;
+    ctx->p_wait_limit = wait_limit;
+    drop_graph(ctx);
+    return SGSPM_OK;
 }
 
 }  // extern "C"

@@ -52,4 +52,9 @@ void ys_go(unsigned nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int
 template <typename T>
 cudaError_t ys_attr(size_t smem);
 
+// Persistent ensemble step (FP32 form, cooperative launch of `grid` CTAs of kThreads threads).
+void persist_go(unsigned grid, size_t smem, cudaStream_t st, const Dev<float>& d, const PersistArgs& a);
+cudaError_t persist_attr(size_t smem);
+int persist_blocks_per_sm(size_t smem);   // resident CTAs per SM at this shared memory, 0 on error
+
 }  // namespace sgspm

@@ -3,6 +3,13 @@
 #pragma once
 #include "passes.cuh"
 
+// Global reads of fields that a pass does not write are marked restrict (read-only path) in the
+// per-pass kernels.  The persistent ensemble kernel runs every pass inside one launch, where a
+// field read in one pass is written in another: its translation unit defines SGSPM_FIELD_RO empty.
+#ifndef SGSPM_FIELD_RO
+#define SGSPM_FIELD_RO __restrict__
+#endif
+
 namespace sgspm {
 
 template <typename T>
@@ -94,7 +101,7 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
 template <int NX>
-__device__ __forceinline__ void slab_load4(float* s, const float* __restrict__ g, int nz, int zs) {
+__device__ __forceinline__ void slab_load4(float* s, const float* SGSPM_FIELD_RO g, int nz, int zs) {
     constexpr int N4 = NX / 4;
     for (int i = threadIdx.x; i < nz * N4; i += blockDim.x) {
         const int z = i / N4, x4 = i - z * N4;
@@ -121,12 +128,12 @@ __device__ __forceinline__ void slab_store4(float* __restrict__ g, const float* 
 //       3 (damping update and projection) compile only the phases of that launch type, so that a
 //       launch fetches and caches far less code (the generic kernel's instruction stream is its
 //       largest stall)
+// One work item of the slab pass (a y row, or rows y0 .. y0 + w - 1 with MULTI) of film wi.x, run
+// by the whole CTA (kThreads threads; dynamic shared memory as laid out by xz_layout).
 template <typename T, int NX, bool ZTC = false, bool MULTI = false, int MODE = 0>
-__global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, XZProg pg, int stray) {
+__device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZProg& pg, int stray) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_launch_dependents();
-    const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
     const int y0 = wi.y, nrow = MULTI ? (wi.z > 0 ? wi.z : 1) : 1;
     // compile-time x lengths (NX >= 8) fold every index division by nx into a shift
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
         auto cell_of = [&](int z, int x) -> long long { return cbase + (z * zstride + x); };
         auto spec_of = [&](int kz, int kx) -> int { return (kz * ny + y) * Kx + kx; };
         // slab <-> field row copies
-        auto load_slab = [&](T* sl, const T* __restrict__ f) {
+        auto load_slab = [&](T* sl, const T* SGSPM_FIELD_RO f) {
             if constexpr (kVec) {
                 slab_load4<NX>(sl, f + cbase, nz, zstride);
             } else {
@@ -308,10 +315,10 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
             if (MODE == 0 && !pg.rhs_dct) { __syncthreads(); continue; }
             // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
             if (MODE != 0 || pg.rhs_copy[ci] < 0) {
-                const T* __restrict__ m1 = d.field[pg.state[0]];
-                const T* __restrict__ m2 = d.field[pg.state[1]];
-                const T* __restrict__ m3 = d.field[pg.state[2]];
-                const T* __restrict__ ma = d.field[pg.state[a]];
+                const T* SGSPM_FIELD_RO m1 = d.field[pg.state[0]];
+                const T* SGSPM_FIELD_RO m2 = d.field[pg.state[1]];
+                const T* SGSPM_FIELD_RO m3 = d.field[pg.state[2]];
+                const T* SGSPM_FIELD_RO ma = d.field[pg.state[a]];
                 // dt (alpha dt), eps and the uniform applied field are split hi + lo in the FP32
                 // form: they set the precession rate in every step, so their FP32 rounding would
                 // act as a fixed perturbation of the parameters (lo parts are zero in FP64)
@@ -776,16 +783,22 @@ __global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* _
     }
 }
 
+template <typename T, int NX, bool ZTC = false, bool MULTI = false, int MODE = 0>
+__global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, const __grid_constant__ XZProg pg,
+                                                          int stray) {
+    pdl_launch_dependents();
+    xz_item<T, NX, ZTC, MULTI, MODE>(d, work[blockIdx.x], pg, stray);
+}
+
 // ------------------------------------------------------------------------------------------
 // Y line pass
 // ------------------------------------------------------------------------------------------
 // NY: compile-time y length of the films this launch covers (0: any length)
+// One work item of the heat line pass: x columns kx0 .. kx0 + tn - 1 of plane kz of film wi.x.
 template <typename T, int NY>
-__global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
+__device__ __forceinline__ void y_heat_item(const Dev<T> d, const int4 wi, const YProg& pg) {
     using V = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_launch_dependents();
-    const int4 wi = work[blockIdx.x];
     const Film F = d.films[wi.x];
     const int kz = wi.y, kx0 = wi.z, tn = wi.w;
     const int nx = F.nx, ny = NY > 0 ? NY : F.ny, nz = F.nz;
@@ -866,6 +879,12 @@ __global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* 
             for (int yy = y_ld; yy < ny; yy += rpp) g[yy * nx + t_ld] = R[t_ld * LR + yy];
         __syncthreads();
     }
+}
+
+template <typename T, int NY>
+__global__ void __launch_bounds__(kThreads) y_heat_kernel(Dev<T> d, const int4* __restrict__ work, const __grid_constant__ YProg pg) {
+    pdl_launch_dependents();
+    y_heat_item<T, NY>(d, work[blockIdx.x], pg);
 }
 
 // pair index of (a, b) in the 6-component symmetric tensor: xx yy zz xy xz yz
@@ -980,15 +999,15 @@ constexpr bool kStrayTwLo = false;
 // order.  Finally the adjoint FFT of each output and a store of y < ny.  Within one step the
 // Gauss-Seidel sweep changes one component between refreshes, so a refresh transforms one
 // input instead of three.
-template <typename T, int NOUT, int E>
-__global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d, const int4* __restrict__ work, YProg pg) {
+// One work item: kx lines kx0 .. kx0 + tn - 1 (tn <= LINES) of plane kz of film wi.x, one warp per
+// line; the CTA has 32 LINES threads.
+template <typename T, int NOUT, int E, int LINES = kWarpLines>
+__device__ __forceinline__ void y_stray_warp_item(const Dev<T> d, const int4 wi, const YProg& pg) {
     using V = cplx<T>;
     constexpr int P = 32 * E, G = 32 / E;
     constexpr int LI = P / 2 + 8;                 // yw_line_stride
     constexpr int HyP = ((P / 2 + 1) + 3) & ~3;   // ktab_row
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_launch_dependents();
-    const int4 wi = work[blockIdx.x];
     const Film& F = d.films[wi.x];
     const int kz = wi.y, kx0 = wi.z, tn = wi.w;
     const int ny = F.ny, Kx = F.Kx, Pz = F.Pz, Hz = Pz / 2 + 1;
@@ -996,8 +1015,8 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
     const bool zodd = kz > Pz / 2;
     tw_t<T>* stw = reinterpret_cast<tw_t<T>*>(smem_raw);
     V* scr0 = reinterpret_cast<V*>(stw + P);
-    V* inb = scr0 + kWarpLines * P;                                       // [3][lines][LI]
-    T* kbuf = reinterpret_cast<T*>(inb + 3 * kWarpLines * LI);            // [3 NOUT][lines][HyP]
+    V* inb = scr0 + LINES * P;                                       // [3][lines][LI]
+    T* kbuf = reinterpret_cast<T*>(inb + 3 * LINES * LI);            // [3 NOUT][lines][HyP]
     stage_async(stw, d.tw + d.plans[F.plan_py].tw, P);
     cp_async_commit();
     cp_async_wait(0);
@@ -1012,7 +1031,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
         if (pg.in_mask & (1 << b)) {
             const V* Sb = d.spec[pg.in_spec[b]] + line0;
             const bool fresh = (pg.fresh_mask >> b) & 1;
-            V* dst = inb + b * kWarpLines * LI;
+            V* dst = inb + b * LINES * LI;
             const int n = fresh ? tn * ny : 0;
             for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
                 const int y = idx / tn, t = idx - y * tn;
@@ -1022,7 +1041,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
             for (int o = 0; o < NOUT; ++o) {
                 const int cc = pair_idx(pg.slot[o], b);
                 const T* src = kt + (((long long)cc * Hz + kzr) * Kx + kx0) * HyP;
-                T* kd = kbuf + (o * 3 + b) * kWarpLines * HyP;
+                T* kd = kbuf + (o * 3 + b) * LINES * HyP;
                 for (int i = threadIdx.x; i < nkch; i += blockDim.x) cp_async_16(kd + i * KCH, src + i * KCH);
             }
         }
@@ -1048,7 +1067,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
         V v[E];
         V* cb = d.ycache + b * d.ycache_n + cline;
         if ((pg.fresh_mask >> b) & 1) {
-            const V* line = inb + (b * kWarpLines + warp) * LI;
+            const V* line = inb + (b * LINES + warp) * LI;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 const int y = lane + 32 * k;
@@ -1068,7 +1087,7 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
             const int cc = pair_idx(pg.slot[o], b);
             const bool yflip = (cc == 3 || cc == 5);
             const bool zflip = (cc == 4 || cc == 5) && zodd;
-            const T* kb = kbuf + ((o * 3 + b) * kWarpLines + warp) * HyP;
+            const T* kb = kbuf + ((o * 3 + b) * LINES + warp) * HyP;
 #pragma unroll
             for (int s1 = 0; s1 < E; ++s1) {
                 const int ky = q + E * (s1 + E * s2);
@@ -1092,6 +1111,13 @@ __global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d,
             if (y < ny) Ho[(long long)y * Kx] = acc[o][k];
         }
     }
+}
+
+template <typename T, int NOUT, int E>
+__global__ void __launch_bounds__(32 * kWarpLines) y_stray_warp_kernel(Dev<T> d, const int4* __restrict__ work,
+                                                                     const __grid_constant__ YProg pg) {
+    pdl_launch_dependents();
+    y_stray_warp_item<T, NOUT, E>(d, work[blockIdx.x], pg);
 }
 
 }  // namespace sgspm

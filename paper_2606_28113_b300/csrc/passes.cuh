@@ -85,9 +85,48 @@ constexpr int kWarpLines = 4;   // kx lines (warps) per CTA of the register stra
 __host__ __device__ inline int yw_line_stride(int Py) { return Py / 2 + 8; }
 
 template <typename T>
-__host__ __device__ inline size_t yw_smem_bytes(int Py, int nout) {
-    return (size_t)Py * sizeof(tw_t<T>) + (size_t)(kWarpLines * Py + 3 * kWarpLines * yw_line_stride(Py)) * sizeof(cplx<T>) +
-           (size_t)3 * nout * kWarpLines * ktab_row(Py) * sizeof(T);
+__host__ __device__ inline size_t yw_smem_bytes(int Py, int nout, int lines = kWarpLines) {
+    return (size_t)Py * sizeof(tw_t<T>) + (size_t)(lines * Py + 3 * lines * yw_line_stride(Py)) * sizeof(cplx<T>) +
+           (size_t)3 * nout * lines * ktab_row(Py) * sizeof(T);
 }
+
+// ---- persistent ensemble step (FP32 form) ------------------------------------------------------
+// One launch runs every pass of a step for all films of a batch.  The passes' work items (slab
+// rows, heat-line tiles, stray-line groups of kPersistLines lines) form one queue in program order
+// (phase by phase, films in order within a phase); CTAs take items from it with a ticket counter.
+// An item of phase q of film f may start once all of film f's items of phases < q are complete: a
+// per-film counter of completed items, waited on with a bounded acquire-spin.  Films never wait on
+// each other, so the tail of one phase of a film overlaps other films' work.
+constexpr int kPersistLines = 8;   // kx lines per stray item (one warp each, kThreads threads)
+
+struct PPhase {
+    int kind;       // 0 slab pass, 1 heat line pass, 2 stray line pass
+    int first;      // index of the phase's first item in the item table
+    int n;          // items of the phase
+    int pad_;
+    XZProg xz;
+    YProg y;
+};
+
+struct PItem {
+    int4 wi;        // work item as the per-pass kernels take it (film, ...)
+    int key;        // size class: x length (slab: 0, 64, 128, 256), y length (heat), E = Py / 32 (stray)
+    int target;     // completed items of the film (within the step) this item waits for
+    int phase;      // index of the item's phase
+    int pad_;
+};
+
+struct PersistArgs {
+    const PPhase* phases;
+    const PItem* items;
+    const int* film_items;     // items of each film in one step
+    unsigned* ctl;             // [0] ticket counter, [1] abandon flag, [2 ..] completed items per film
+    int nphase;
+    int items_per_step;
+    int nsteps;                // steps in this launch
+    int stray;
+    long long wait_limit;      // clock cycles one dependency wait may take before the launch is abandoned
+    int withhold;              // test switch: the ticket whose item is skipped (never completes), or -1
+};
 
 }  // namespace sgspm

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libsgspm.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, GSPM, NO_STRAY, FROZEN_STRAY, NO_GRAPH, TF32X3 = 1, 2, 4, 8, 16, 32
+FP64, GSPM, NO_STRAY, FROZEN_STRAY, NO_GRAPH, TF32X3, PERSISTENT = 1, 2, 4, 8, 16, 32, 64
 M, HE, HS = 0, 1, 2
 F32, F64 = 0, 1
 FORCE_NONE, FORCE_MMS_1D, FORCE_MMS_3D = 0, 1, 3
@@ -68,6 +68,7 @@ def lib():
     L.sgspm_last_error.restype = ctypes.c_char_p
     L.sgspm_launches_per_step.argtypes = [vp]
     L.sgspm_test_tc_timeout.argtypes = [vp, i, i]
+    L.sgspm_test_persist_wait.argtypes = [vp, i, ll]
     L.sgspm_fp64_fma_peak.argtypes = [dp]
     L.sgspm_profile_step.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int), i]
     L.sgspm_version.argtypes = []
@@ -84,7 +85,7 @@ def lib():
                  "sgspm_set_field",
                  "sgspm_get_field", "sgspm_step", "sgspm_energy", "sgspm_set_forcing", "sgspm_set_time",
                  "sgspm_get_time", "sgspm_sync", "sgspm_destroy", "sgspm_launches_per_step", "sgspm_version",
-                 "sgspm_test_tc_timeout", "sgspm_fp64_fma_peak",
+                 "sgspm_test_tc_timeout", "sgspm_test_persist_wait", "sgspm_fp64_fma_peak",
                  "sgspm_profile_step"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -112,7 +113,7 @@ def _buffer(x):
     return ctypes.c_void_p(a.ctypes.data), (F64 if a.dtype == np.float64 else F32), a
 
 
-def _flags(fp64, scheme, stray, refresh, graph, tf32x3=False):
+def _flags(fp64, scheme, stray, refresh, graph, tf32x3=False, persistent=False):
     f = 0
     if tf32x3:
         f |= TF32X3
@@ -130,6 +131,8 @@ def _flags(fp64, scheme, stray, refresh, graph, tf32x3=False):
         raise ValueError(refresh)
     if not graph:
         f |= NO_GRAPH
+    if persistent:
+        f |= PERSISTENT
     return f
 
 
@@ -149,7 +152,7 @@ class Handle:
     """A handle of one film or of a batch of films (sgspm_create / sgspm_create_batch)."""
 
     def __init__(self, films, fp64=False, scheme="sgspm", stray=True, refresh="R1", graph=True, stream=None,
-                 tf32x3=False):
+                 tf32x3=False, persistent=False):
         L = lib()
         self.films = [dict(f) for f in films]
         nf = len(self.films)
@@ -158,7 +161,7 @@ class Handle:
         self._eps, self._Q, self._alpha, self._dt = arr("eps"), arr("Q"), arr("alpha"), arr("dt")
         self._u = np.ascontiguousarray([f.get("u", (1.0, 0.0, 0.0)) for f in self.films], dtype=np.float64).reshape(-1)
         self.fp64 = fp64
-        self.flags = _flags(fp64, scheme, stray, refresh, graph, tf32x3)
+        self.flags = _flags(fp64, scheme, stray, refresh, graph, tf32x3, persistent)
         h = ctypes.c_void_p()
         rc = L.sgspm_create_batch(nf, grids, _dptr(self._eps), _dptr(self._Q), _dptr(self._alpha), _dptr(self._dt),
                                   _dptr(self._u), self.flags, _stream(stream), ctypes.byref(h))
@@ -315,6 +318,10 @@ class Handle:
 
     def launches_per_step(self):
         return lib().sgspm_launches_per_step(self.h)
+
+    def test_persist_wait(self, withhold=-1, wait_limit=4000000000):
+        """Test support (persistent step): skip one work item so that the waits behind it run out."""
+        self._check(lib().sgspm_test_persist_wait(self.h, int(withhold), int(wait_limit)))
 
     def test_tc_timeout(self, skip_mma, wait_limit=0):
         """Test support (TF32X3 form): skip the tensor-core MMAs so that their bounded waits run out."""

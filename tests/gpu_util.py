@@ -39,3 +39,26 @@ def gpu_run(m0, steps, chunk=None, energies=False, **kw):
     m = H.split(H.get_m())[0]
     H.close()
     return (m, np.array(E)) if energies else m
+
+
+def oracle_response(m0, ref, steps, rel, seed=1, **kw):
+    """How far the oracle's own trajectory (ref after `steps` steps from m0) moves when its input
+    is perturbed by `rel` relative, with a random sign per entry."""
+    rng = np.random.default_rng(seed)
+    b, _ = oracle_run(m0 * (1 + rel * rng.choice([-1, 1], size=m0.shape)), steps=steps, **kw)
+    return float(np.abs(b - ref).max())
+
+
+def oracle_noise_response(m0, ref, steps, rel, seed=2, n=None, h=None, eps=None, Q=None, alpha=None, dt=None,
+                          u=(1.0, 0.0, 0.0), he=(0.0, 0.0, 0.0)):
+    """How far the oracle's trajectory moves when its state is perturbed by `rel` relative (random
+    sign per entry) after every step: the response to rounding of that size made in every step."""
+    o = scheme.Oracle(scheme.Params(n=n, h=h, eps=eps, Q=Q, alpha=alpha, dt=dt, u=u, he=he))
+    rng = np.random.default_rng(seed)
+    m = m0.copy()
+    t = 0.0
+    for _ in range(steps):
+        m = o.step(m, t)
+        t += dt
+        m = m * (1 + rel * rng.choice([-1, 1], size=m.shape))
+    return float(np.abs(m - ref).max())
