@@ -167,7 +167,7 @@ def run_reference(args):
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands (cold
 # caches, full metric set, 256x256x8 film).  Only valid for the kernel that was captured: set an
 # entry back to None when its kernel changes.
-NCU_TRAFFIC = {1: 17.5e6}   # slab pass, right-hand-side launch (kind 1), 256x256x8 FP32
+NCU_TRAFFIC = {}   # kind -> bytes; empty while no capture of the current kernels is recorded
 
 
 # algorithmic bytes per cell of each launch kind, FP32: every operator reads its real operand
@@ -413,44 +413,46 @@ def run_gpu(args):
     step_frac = 292.0 * value / world / (hbm * 1e9) if hbm else None
 
     # ---- accuracy of the FP32 form against the FP64 form on the same GPU --------------------
-    nacc = min(args.steps, 200)
-    Ha = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
-                    stream=stream.cuda_stream)
-    Hb = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=True,
-                    stream=stream.cuda_stream)
-    Hc = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
-                    stream=stream.cuda_stream, tf32x3=True)
-    Ha.set_m(m0)
-    Hb.set_m(m0)
-    Hc.set_m(m0)
-    Ha.step(nacc)
-    evc = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    Hc.step(2)
-    Hc.sync()
-    evc[0].record(stream)
-    Hc.step(nacc - 2)
-    evc[1].record(stream)
-    Hc.sync()
-    tc_ms = evc[0].elapsed_time(evc[1]) / (nacc - 2)
-    ev64 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    Hb.step(2)
-    Hb.sync()
-    ev64[0].record(stream)
-    Hb.step(nacc - 2)
-    ev64[1].record(stream)
-    Hb.sync()
-    fp64_ms = ev64[0].elapsed_time(ev64[1]) / (nacc - 2)
-    ma, mb, mc = Ha.get_m(), Hb.get_m(), Hc.get_m()
-    Ea, Eb, Ec = Ha.energy()[0], Hb.energy()[0], Hc.energy()[0]
-    Ha.close()
-    Hb.close()
-    Hc.close()
-    tc_form = {"ms_per_step": tc_ms, "value": ncell / (tc_ms / 1e3), "unit": UNIT,
-               "accuracy_vs_fp64_form": {"steps": nacc, "max_abs_dm": float(np.abs(mc - mb).max()),
-                                         "rel_energy_err": float(abs(Ec[4] - Eb[4]) / abs(Eb[4]))},
-               "note": "not L2-flushed; z DCTs as 3xTF32 GEMMs on tcgen05"}
-    max_dm = float(np.abs(ma - mb).max())
-    rel_e = float(abs(Ea[4] - Eb[4]) / abs(Eb[4]))
+    tc_form = fp64_ms = max_dm = rel_e = None
+    if args.side:
+        nacc = min(args.steps, 200)
+        Ha = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
+                        stream=stream.cuda_stream)
+        Hb = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=True,
+                        stream=stream.cuda_stream)
+        Hc = sgspm.film(w["n"], w["h"], w["eps"], w["Q"], w["alpha"], w["dt"], u=w["u"], he=w["he"], fp64=False,
+                        stream=stream.cuda_stream, tf32x3=True)
+        Ha.set_m(m0)
+        Hb.set_m(m0)
+        Hc.set_m(m0)
+        Ha.step(nacc)
+        evc = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        Hc.step(2)
+        Hc.sync()
+        evc[0].record(stream)
+        Hc.step(nacc - 2)
+        evc[1].record(stream)
+        Hc.sync()
+        tc_ms = evc[0].elapsed_time(evc[1]) / (nacc - 2)
+        ev64 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        Hb.step(2)
+        Hb.sync()
+        ev64[0].record(stream)
+        Hb.step(nacc - 2)
+        ev64[1].record(stream)
+        Hb.sync()
+        fp64_ms = ev64[0].elapsed_time(ev64[1]) / (nacc - 2)
+        ma, mb, mc = Ha.get_m(), Hb.get_m(), Hc.get_m()
+        Ea, Eb, Ec = Ha.energy()[0], Hb.energy()[0], Hc.energy()[0]
+        Ha.close()
+        Hb.close()
+        Hc.close()
+        tc_form = {"ms_per_step": tc_ms, "value": ncell / (tc_ms / 1e3), "unit": UNIT,
+                   "accuracy_vs_fp64_form": {"steps": nacc, "max_abs_dm": float(np.abs(mc - mb).max()),
+                                             "rel_energy_err": float(abs(Ec[4] - Eb[4]) / abs(Eb[4]))},
+                   "note": "not L2-flushed; z DCTs as 3xTF32 GEMMs on tcgen05"}
+        max_dm = float(np.abs(ma - mb).max())
+        rel_e = float(abs(Ea[4] - Eb[4]) / abs(Eb[4]))
 
     # ---- end to end through the C ABI with host buffers -------------------------------------
     host_in = torch.from_numpy(m0.astype(np.float32).reshape(-1)).pin_memory()
@@ -476,7 +478,7 @@ def run_gpu(args):
                  "tf32x3": run_strip(sgspm, torch, stream, args.strip_steps, tf32x3=True)}
         chosen = min(forms, key=lambda k: forms[k]["ms_per_step"])
         strip = dict(forms[chosen], chosen_form=chosen, other_form=forms["tf32x3" if chosen == "fp32" else "fp32"])
-    fma64 = sgspm.fp64_fma_peak()
+    fma64 = sgspm.fp64_fma_peak() if args.side else None
 
     if rank == 0:
         cpu, _ = cpu_baseline(w, m0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else (None, None)
@@ -490,13 +492,15 @@ def run_gpu(args):
                            "autotuned": tuned},
                 "roofline": roof,
                 "step_algorithmic_hbm_frac": step_frac,
-                "fp64_form": {"ms_per_step": fp64_ms, "value": ncell / (fp64_ms / 1e3), "unit": UNIT,
-                              "note": "the same fused slab/line kernels in double (runtime-length variants), L2 not flushed",
-                              "step_algorithmic_hbm_frac": (584.0 * ncell / (fp64_ms / 1e3) / (hbm * 1e9)) if hbm else None,
-                              "fp64_fma_peak_gflops": fma64},
-                "speedup_vs_fp64_form": (fp64_ms / (step_ms / args.steps)),
+                "fp64_form": None if fp64_ms is None else {
+                    "ms_per_step": fp64_ms, "value": ncell / (fp64_ms / 1e3), "unit": UNIT,
+                    "note": "the same fused slab/line kernels in double (runtime-length variants), L2 not flushed",
+                    "step_algorithmic_hbm_frac": (584.0 * ncell / (fp64_ms / 1e3) / (hbm * 1e9)) if hbm else None,
+                    "fp64_fma_peak_gflops": fma64},
+                "speedup_vs_fp64_form": None if fp64_ms is None else (fp64_ms / (step_ms / args.steps)),
                 "tf32x3_form": tc_form,
-                "accuracy_vs_fp64_form": {"steps": nacc, "max_abs_dm": max_dm, "rel_energy_err": rel_e},
+                "accuracy_vs_fp64_form": None if max_dm is None else {"steps": min(args.steps, 200), "max_abs_dm": max_dm,
+                                                                       "rel_energy_err": rel_e},
                 "launch_shares": {str(k): v / total for k, v in sorted(share.items())},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * ncell * 4,
@@ -523,6 +527,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps for cpu_baseline (0: skip)")
     ap.add_argument("--autotune", type=int, default=1,
                     help="choose launch shapes of the timed film with sgspm_autotune before timing (0: defaults)")
+    ap.add_argument("--side", type=int, default=1,
+                    help="also run the FP64 and TF32X3 forms of the film (accuracy, speed-up) and the FP64 FMA probe (0: skip)")
     ap.add_argument("--small-configs", type=int, default=1,
                     help="also time the 32x32x4 FP64 film and the 128x128x4 adjoint (0: skip)")
     ap.add_argument("--strip-steps", type=int, default=400,
