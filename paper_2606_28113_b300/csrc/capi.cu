@@ -99,6 +99,7 @@ struct sgspm_ctx {
         int n;
         size_t smem;
         int rows = 1;                  // slab pass: y rows per CTA (batch packing)
+        bool nz8 = true;               // slab pass: every film of the class has nz = kZReg
     };
     std::vector<KClass> xz_cls, yh_cls, yw_cls;
     int4* d_work_xz = nullptr;
@@ -274,7 +275,7 @@ static void launch_xz_mode(int mode, int nb, size_t smem, cudaStream_t st, const
 
 template <typename T>
 static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray,
-                      bool tf32x3, int rows) {
+                      bool tf32x3, int rows, bool nz8) {
     if constexpr (sizeof(T) == 8) {   // the FP64 form uses the runtime-length kernel only
         xz_go<T, 0, false, false>(nb, smem, st, d, w, pg, stray);
         return;
@@ -294,7 +295,8 @@ static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T
                 default: xz_go<T, 512, true, false>(nb, smem, st, d, w, pg, stray); return;
             }
         }
-        const int mode = xz_mode(pg);
+        // the 512-thread launch types of the 256-wide class run slabs of nz = kZReg only
+        const int mode = (key == 256 && !nz8) ? 0 : xz_mode(pg);
         switch (key) {
             case 64: launch_xz_mode<T, 64>(mode, nb, smem, st, d, w, pg, stray); return;
             case 128: launch_xz_mode<T, 128>(mode, nb, smem, st, d, w, pg, stray); return;
@@ -423,7 +425,7 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
     switch (L.kind) {
         case 0:
             for (const auto& c : ctx->xz_cls)
-                launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3, c.rows);
+                launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3, c.rows, c.nz8);
             break;
         case 1:
             for (const auto& c : ctx->yh_cls) launch_yh<T>(c.key, c.n, c.smem, st, d, c.work, L.y, ctx->heat_threads);
@@ -1426,6 +1428,8 @@ static int setup_t(sgspm_ctx* ctx) {
         }
         for (auto& kv : wx) {
             sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), sxk[kv.first]};
+            for (const Film& F : ctx->films)
+                if (xz_key(sizeof(T) == 8, F) == c.key && F.nz != kZReg) c.nz8 = false;
             if ((rc = up4(&c.work, kv.second))) return rc;
             CK(attr_xz<T>(c.key, c.smem, ctx->tf32x3));
             ctx->xz_cls.push_back(c);

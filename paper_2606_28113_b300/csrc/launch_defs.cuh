@@ -8,7 +8,7 @@ namespace sgspm {
 
 template <typename T, int NX, bool ZTC, bool MULTI, int MODE>
 void xz_go(unsigned nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray) {
-    launch_pdl(xz_kernel<T, NX, ZTC, MULTI, MODE>, nb, kThreads, smem, st, d, w, pg, stray);
+    launch_pdl(xz_kernel<T, NX, ZTC, MULTI, MODE>, nb, xz_nt<NX, MODE, MULTI, ZTC>(), smem, st, d, w, pg, stray);
 }
 template <typename T, int NX, bool ZTC, bool MULTI, int MODE>
 cudaError_t xz_attr(size_t smem) {

@@ -137,13 +137,19 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
     const Film F = d.films[wi.x];
     const int y0 = wi.y, nrow = MULTI ? (wi.z > 0 ? wi.z : 1) : 1;
     // compile-time x lengths (NX >= 8) fold every index division by nx into a shift
-    const int nx = NX > 0 ? NX : F.nx, ny = F.ny, nz = F.nz;
-    const int Px = NX > 0 ? 2 * NX : F.Px, Pz = F.Pz, Kx = NX > 0 ? NX + 1 : F.Kx;
+    // the 512-thread kernels run films with nz = kZReg only (the host dispatches others elsewhere)
+    constexpr bool kPairK = xz_nt<NX, MODE, MULTI, ZTC>() == 2 * kThreads;
+    const int nx = NX > 0 ? NX : F.nx, ny = F.ny, nz = kPairK ? kZReg : F.nz;
+    const int Px = NX > 0 ? 2 * NX : F.Px, Pz = kPairK ? 2 * kZReg : F.Pz, Kx = NX > 0 ? NX + 1 : F.Kx;
     const XZLayout Lo = xz_layout(nx, nz, Px, Pz, Kx, stray != 0, ZTC);
     // the zero-padded x transform (Px = 2 NX) as two NX-point FFTs per line pair
     constexpr bool kHalfX = NX >= 64 && NX <= 512;
     // four-cell loads and stores of the pointwise phases (FP32, compile-time x length)
     constexpr bool kVec = NX >= 8 && sizeof(T) == 4;
+    // lane pairs share each column's register z transforms (512-thread kernels): the padded DFTs
+    // split into even and odd kz (two 8-point transforms), the dense DCTs into halves of the outputs
+    constexpr bool kPair = kPairK;
+    const int pr = threadIdx.x & 1;   // lane of the pair
     __shared__ Plan pdx, pdz, ppx, ppz;
     if (threadIdx.x == 0) {
         // pre-staged plan copies (their twiddle offsets refer to the shared layout below)
@@ -235,7 +241,42 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
                 __syncthreads();
             } else if (pg.rhs_h[ci] >= 0 && stray) {
                 const V* H = d.spec[pg.rhs_h[ci]] + sbase;
-                if (zreg) {
+                if (kPair && nz == 8) {
+                    // inverse zero-padded DFT along z (Pz = 16), one lane pair per kx column: lane r
+                    // transforms the inputs kz = 2j + r (lane 1 then multiplies by W16^-z), the pair
+                    // swaps halves, and lane r keeps the outputs z = 4r .. 4r + 3
+                    for (int base = 0; base < Kx; base += (int)blockDim.x / 2) {
+                        if (base + ((int)threadIdx.x & ~31) / 2 >= Kx) continue;   // whole warp idle
+                        const int kx = base + ((int)threadIdx.x >> 1);
+                        const bool act = kx < Kx;
+                        V v[8];
+    #pragma unroll
+                        for (int j = 0; j < 8; ++j) v[j] = act ? H[spec_of(2 * j + pr, kx)] : cmk<V>(T(0), T(0));
+                        Bfly<8, true, V>::run(v);
+                        if (pr) {
+    #pragma unroll
+                            for (int z = 1; z < 8; ++z) v[z] = twmul<true>(v[z], twz[z]);
+                        }
+                        V acc[4];
+    #pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const V snd = pr ? v[i] : v[4 + i];   // the half the partner keeps
+                            V rcv;
+                            rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1);
+                            rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1);
+                            acc[i] = pr ? cadd(rcv, v[4 + i]) : cadd(v[i], rcv);
+                        }
+                        if (act) {
+    #pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const int p = 2 * pr + q;
+                                if constexpr (kHalfX) c2r_put_h<T>(xw0, p, kx, Px, acc[2 * q], acc[2 * q + 1]);
+                                else c2r_put<T>(xw0, p, kx, Px, acc[2 * q], acc[2 * q + 1]);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                } else if (zreg) {
                     // inverse zero-padded DFT along z in registers, one thread per kx column
                     for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
                         V acc[kZReg];
@@ -453,6 +494,26 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
                 }
             }
             if (zdone) {
+            } else if (kPair && zreg) {
+                // lane pairs per x column: lane r computes the outputs k = r kh .. of the column
+                const int kh = (nz + 1) / 2;
+                for (int x = (int)threadIdx.x >> 1; x < nx; x += (int)blockDim.x / 2) {
+                    T v[kZReg];
+    #pragma unroll
+                    for (int z = 0; z < kZReg; ++z) v[z] = z < nz ? h[z * nx + x] : T(0);
+                    __syncwarp();
+    #pragma unroll
+                    for (int kk = 0; kk < kZReg / 2; ++kk) {
+                        const int k = pr * kh + kk;
+                        if (kk >= kh || k >= nz) break;
+                        T acc = T(0);
+    #pragma unroll
+                        for (int z = 0; z < kZReg; ++z)
+                            if (z < nz) acc += Cz[k * nz + z] * v[z];
+                        h[k * nx + x] = acc;
+                    }
+                }
+                __syncthreads();
             } else if (zreg) {
                 for (int x = threadIdx.x; x < nx; x += blockDim.x) {
                     T v[kZReg];
@@ -490,6 +551,26 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
                 }
             }
             if (zdone) {
+            } else if (kPair && zreg) {
+                // lane pairs per x column: lane r computes the outputs z = r kh .. of the column
+                const int kh = (nz + 1) / 2;
+                for (int x = (int)threadIdx.x >> 1; x < nx; x += (int)blockDim.x / 2) {
+                    T v[kZReg];
+    #pragma unroll
+                    for (int k = 0; k < kZReg; ++k) v[k] = k < nz ? s[k * nx + x] : T(0);
+                    __syncwarp();
+    #pragma unroll
+                    for (int zz = 0; zz < kZReg / 2; ++zz) {
+                        const int z = pr * kh + zz;
+                        if (zz >= kh || z >= nz) break;
+                        T acc = T(0);
+    #pragma unroll
+                        for (int k = 0; k < kZReg; ++k)
+                            if (k < nz) acc += Czi[z * nz + k] * v[k];
+                        s[z * nx + x] = acc;
+                    }
+                }
+                __syncthreads();
             } else if (zreg) {
                 for (int x = threadIdx.x; x < nx; x += blockDim.x) {
                     T v[kZReg];
@@ -732,7 +813,23 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
                     else return r2c_get<T>(r, line, k, Px);
                 };
                 V* out = d.spec[pg.fwd_dst[i]] + sbase;
-                if (zreg) {
+                if (kPair && nz == 8) {
+                    // zero-padded DFT along z (Pz = 16), one lane pair per kx column: lane r computes
+                    // the outputs kz = 2j + r as the 8-point DFT of v (r = 0) or of v W16^z (r = 1)
+                    for (int kx = (int)threadIdx.x >> 1; kx < Kx; kx += (int)blockDim.x / 2) {
+                        V v[8];
+    #pragma unroll
+                        for (int z = 0; z < 8; ++z) v[z] = rget(z, kx);
+                        if (pr) {
+    #pragma unroll
+                            for (int z = 1; z < 8; ++z) v[z] = twmul(v[z], twz[z]);
+                        }
+                        Bfly<8, false, V>::run(v);
+    #pragma unroll
+                        for (int j = 0; j < 8; ++j) out[spec_of(2 * j + pr, kx)] = v[j];
+                    }
+                    __syncthreads();
+                } else if (zreg) {
                     // zero-padded DFT along z in registers, one thread per kx column
                     for (int kx = threadIdx.x; kx < Kx; kx += blockDim.x) {
                         V v[2 * kZReg];
@@ -784,8 +881,8 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
 }
 
 template <typename T, int NX, bool ZTC = false, bool MULTI = false, int MODE = 0>
-__global__ void __launch_bounds__(kThreads, 2) xz_kernel(Dev<T> d, const int4* __restrict__ work, const __grid_constant__ XZProg pg,
-                                                          int stray) {
+__global__ void __launch_bounds__((xz_nt<NX, MODE, MULTI, ZTC>()), 2) xz_kernel(Dev<T> d, const int4* __restrict__ work,
+                                                                                const __grid_constant__ XZProg pg, int stray) {
     pdl_launch_dependents();
     xz_item<T, NX, ZTC, MULTI, MODE>(d, work[blockIdx.x], pg, stray);
 }

@@ -23,6 +23,14 @@ struct XZLayout {
     int tc;    // bytes of the tensor-core B operands (TF32X3 form), 16-byte aligned, else 0
 };
 
+// Threads of a slab-pass CTA.  The Gauss-Seidel and right-hand-side launch types of the 256-wide
+// slabs run 512 (64 registers each): every pointwise, staging and packing loop of a row is split
+// over twice as many threads, and the register z transforms run on lane pairs (see xz_item).
+template <int NX, int MODE, bool MULTI, bool ZTC>
+__host__ __device__ constexpr int xz_nt() {
+    return (NX == 256 && (MODE == 1 || MODE == 2) && !MULTI && !ZTC) ? 2 * kThreads : kThreads;
+}
+
 // Thin films (nz <= kZReg) transform along z in registers, one thread per column: dense
 // DCT-II / DCT-III (nz x nz tables) and the zero-padded DFT of length Pz <= 2 kZReg.
 constexpr int kZReg = 8;
