@@ -28,7 +28,7 @@ struct XZLayout {
 // over twice as many threads, and the register z transforms run on lane pairs (see xz_item).
 template <int NX, int MODE, bool MULTI, bool ZTC>
 __host__ __device__ constexpr int xz_nt() {
-    return (NX == 256 && (MODE == 1 || MODE == 2) && !MULTI && !ZTC) ? 2 * kThreads : kThreads;
+    return (NX == 256 && (MODE == 1 || MODE == 2 || MODE == 3) && !MULTI && !ZTC) ? 2 * kThreads : kThreads;
 }
 
 // Thin films (nz <= kZReg) transform along z in registers, one thread per column: dense
