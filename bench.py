@@ -167,9 +167,10 @@ def run_reference(args):
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands (cold
 # caches, full metric set, 256x256x8 film).  Only valid for the kernel that was captured: set an
 # entry back to None when its kernel changes.
-# slab pass, right-hand-side launches (kind 1), 256x256x8 FP32: mean over the 6 launches of a step of
-# the captured 23.27 MB (2 components) and 14.84 MB (1 component), +8.42 MB per component
-NCU_TRAFFIC = {1: 19.06e6}
+# slab pass, right-hand-side launches (kind 1), 256x256x8 FP32, 512-thread kernel: mean over the 6
+# launches of a step of the captured 34.47 MB (2 components) and 22.72 MB (1 component), read + write,
+# +11.75 MB per component
+NCU_TRAFFIC = {1: 28.6e6}
 
 
 # algorithmic bytes per cell of each launch kind, FP32: every operator reads its real operand
