@@ -22,10 +22,13 @@ template <typename T>
 __device__ __forceinline__ void film_cell(const Dev<T>& d, const int4& wi, int i, long long& c, int& x, int& y, int& z,
                                           const Film*& F) {
     F = &d.films[wi.x];
-    const long long loc = wi.y + (long long)i;
-    x = (int)(loc % F->nx);
-    y = (int)((loc / F->nx) % F->ny);
-    z = (int)(loc / ((long long)F->nx * F->ny));
+    // in-film offsets fit 32 bits (films are limited to 2^29 cells): 32-bit divisions
+    const int loc = wi.y + i;
+    const int nx = F->nx, sxy = F->nx * F->ny;
+    z = loc / sxy;
+    const int r = loc - z * sxy;
+    y = r / nx;
+    x = r - y * nx;
     c = F->off_cell + loc;
 }
 
@@ -79,8 +82,8 @@ __global__ void __launch_bounds__(kThreads) adj_f_kernel(Dev<T> d, const int4* _
     const T u[3] = {T(F.u[0]), T(F.u[1]), T(F.u[2])};
     const long long sxy = (long long)nx * ny;
     for (int i = threadIdx.x; i < wi.z; i += blockDim.x) {
-        const long long loc = wi.y + (long long)i;
-        const int x = (int)(loc % nx), y = (int)((loc / nx) % ny), z = (int)(loc / sxy);
+        const int loc = wi.y + i;
+        const int z = loc / (int)sxy, r = loc - z * (int)sxy, y = r / nx, x = r - y * nx;
         const long long c = F.off_cell + loc;
         T fb[3] = {T(0), T(0), T(0)};
         for (int k = 0; k < a.n; ++k) {
@@ -167,11 +170,11 @@ __global__ void __launch_bounds__(kThreads) adj_alpha_partial_kernel(Dev<T> d, c
     const Film& F = d.films[wi.x];
     const int nx = F.nx, ny = F.ny, nz = F.nz;
     const long long sxy = (long long)nx * ny;
-    const double ihx = 1.0 / (F.hx * F.hx), ihy = 1.0 / (F.hy * F.hy), ihz = 1.0 / (F.hz * F.hz);
+    const double ihx = F.ih2[0], ihy = F.ih2[1], ihz = F.ih2[2];
     double acc = 0.0;
     for (int i = threadIdx.x; i < wi.z; i += blockDim.x) {
-        const long long loc = wi.y + (long long)i;
-        const int x = (int)(loc % nx), y = (int)((loc / nx) % ny), z = (int)(loc / sxy);
+        const int loc = wi.y + i;
+        const int z = loc / (int)sxy, r = loc - z * (int)sxy, y = r / nx, x = r - y * nx;
         const long long c = F.off_cell + loc;
         double e[3];
         for (int k = 0; k < 3; ++k) e[k] = (double)d.field[a.e[k]][c];

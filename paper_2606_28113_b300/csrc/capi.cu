@@ -1424,7 +1424,8 @@ static int setup_t(sgspm_ctx* ctx) {
             sxk[kx] = std::max(sxk[kx], xz_smem_bytes<T>(L));
             first_e.push_back((int)we.size());
             long long nc = (long long)F.nx * F.ny * F.nz;
-            for (long long c0 = 0; c0 < nc; c0 += 4096) we.push_back(make_int4(f, (int)c0, (int)std::min(4096LL, nc - c0), 0));
+            // pointwise and reduction kernels (energy, adjoint): items of 1024 cells, 4 per thread
+            for (long long c0 = 0; c0 < nc; c0 += 1024) we.push_back(make_int4(f, (int)c0, (int)std::min(1024LL, nc - c0), 0));
         }
         for (auto& kv : wx) {
             sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), sxk[kv.first]};

@@ -132,6 +132,7 @@ struct Film {
     float fs_Q;              // Q
     float fs_u[3];           // easy axis
     float fs_ih[3];          // 1 / h_a^2
+    double ih2[3];           // 1 / h_a^2 (FP64)
 };
 
 // Fill the FP32 parameter fields of a film from its FP64 parameters (host).
@@ -149,6 +150,9 @@ inline void film_consts(Film& F) {
     split(1.0 / ((double)F.nx * F.ny * F.nz), F.fs_n);
     F.fs_Q = (float)F.Q;
     for (int a = 0; a < 3; ++a) F.fs_u[a] = (float)F.u[a];
+    F.ih2[0] = 1.0 / (F.hx * F.hx);
+    F.ih2[1] = 1.0 / (F.hy * F.hy);
+    F.ih2[2] = 1.0 / (F.hz * F.hz);
     F.fs_ih[0] = (float)(1.0 / (F.hx * F.hx));
     F.fs_ih[1] = (float)(1.0 / (F.hy * F.hy));
     F.fs_ih[2] = (float)(1.0 / (F.hz * F.hz));

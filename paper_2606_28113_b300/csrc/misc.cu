@@ -19,18 +19,17 @@ __global__ void __launch_bounds__(kThreads) energy_partial_kernel(Dev<T> d, cons
     const T* m[3] = {d.field[m0], d.field[m0 + 1], d.field[m0 + 2]};
     double ex = 0, an = 0, st = 0, ze = 0;
     for (int i = threadIdx.x; i < wi.z; i += blockDim.x) {
-        long long loc = wi.y + i;
-        int x = loc % nx;
-        int y = (loc / nx) % ny;
-        int z = loc / sxy;
+        const int loc = wi.y + i;   // in-film offset (32 bits)
+        const int z = loc / (int)sxy, r = loc - z * (int)sxy;
+        const int y = r / nx, x = r - y * nx;
         long long c = F.off_cell + loc;
         const T* ml[3] = {d.flo[m0], d.flo[m0 + 1], d.flo[m0 + 2]};
         auto val = [&](int a, long long cc) -> double { return (double)m[a][cc] + (ml[a] ? (double)ml[a][cc] : 0.0); };
         double v[3] = {val(0, c), val(1, c), val(2, c)};
         for (int a = 0; a < 3; ++a) {
-            if (x + 1 < nx) { double q = val(a, c + 1) - v[a]; ex += q * q / (F.hx * F.hx); }
-            if (y + 1 < ny) { double q = val(a, c + nx) - v[a]; ex += q * q / (F.hy * F.hy); }
-            if (z + 1 < nz) { double q = val(a, c + sxy) - v[a]; ex += q * q / (F.hz * F.hz); }
+            if (x + 1 < nx) { double q = val(a, c + 1) - v[a]; ex += q * q * F.ih2[0]; }
+            if (y + 1 < ny) { double q = val(a, c + nx) - v[a]; ex += q * q * F.ih2[1]; }
+            if (z + 1 < nz) { double q = val(a, c + sxy) - v[a]; ex += q * q * F.ih2[2]; }
         }
         double mu = v[0] * F.u[0] + v[1] * F.u[1] + v[2] * F.u[2];
         an += v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - mu * mu;
