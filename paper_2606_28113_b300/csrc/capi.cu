@@ -136,6 +136,8 @@ struct sgspm_ctx {
     int p_withhold = -1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t adj_graph = nullptr;       // reverse step: forward transform, recording step, adjoint step
+    cudaGraphExec_t adj_gexec = nullptr;
     bool have_m = false;
     bool forcing = false;
     long long steps = 0;
@@ -953,8 +955,33 @@ static int upload_tables(sgspm_ctx* ctx) {
 static int drop_graph(sgspm_ctx* ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->adj_gexec) cudaGraphExecDestroy(ctx->adj_gexec);
+    if (ctx->adj_graph) cudaGraphDestroy(ctx->adj_graph);
     ctx->gexec = nullptr;
     ctx->graph = nullptr;
+    ctx->adj_gexec = nullptr;
+    ctx->adj_graph = nullptr;
+    return SGSPM_OK;
+}
+
+// The launches of one reverse step (the state's forward transform, the recording step and the
+// adjoint step) captured once into a CUDA graph; the caller loads the step's state before each
+// launch of it.
+static int capture_reverse(sgspm_ctx* ctx) {
+    if (ctx->adj_gexec) return SGSPM_OK;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = run_prog(ctx, ctx->fwd_prog, ctx->cap);
+    if (!rc) rc = run_prog(ctx, ctx->rec_prog, ctx->cap);
+    if (!rc) rc = run_prog(ctx, ctx->adj_prog, ctx->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    ctx->adj_graph = g;
+    CK(cudaGraphInstantiate(&ctx->adj_gexec, g, 0));
     return SGSPM_OK;
 }
 
@@ -1761,13 +1788,22 @@ static int grad_t(sgspm_ctx* ctx, const void* dL_dmT, int dtype, void* dL_dhe, d
         // recompute the segment's step states
         if ((rc = state_io<T>(ctx, ck + sgi * per, false))) return rc;
         if ((rc = run_prog(ctx, ctx->fwd_prog, ctx->stream))) return rc;
+        const bool graphs = !(ctx->flags & SGSPM_NO_GRAPH);
+        if (graphs && !ctx->gexec && (rc = capture_step(ctx))) return rc;
         for (long long j = 0; j < L; ++j) {
             if ((rc = state_io<T>(ctx, sg + j * per, true))) return rc;
-            if (j + 1 < L && (rc = run_prog(ctx, ctx->step_prog, ctx->stream))) return rc;
+            if (j + 1 == L) break;
+            if (graphs) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            else if ((rc = run_prog(ctx, ctx->step_prog, ctx->stream))) return rc;
         }
         // reverse through the segment
+        if (graphs && (rc = capture_reverse(ctx))) return rc;
         for (long long j = L - 1; j >= 0; --j) {
             if ((rc = state_io<T>(ctx, sg + j * per, false))) return rc;
+            if (graphs) {
+                CK(cudaGraphLaunch(ctx->adj_gexec, ctx->stream));
+                continue;
+            }
             if ((rc = run_prog(ctx, ctx->fwd_prog, ctx->stream))) return rc;
             if ((rc = run_prog(ctx, ctx->rec_prog, ctx->stream))) return rc;
             if ((rc = run_prog(ctx, ctx->adj_prog, ctx->stream))) return rc;
