@@ -262,9 +262,10 @@ int sgspm_test_persist_wait(sgspm_t h, int withhold, long long wait_limit);
  * call shares that array: calls that overlap on the GPU (unordered streams) race on it and
  * must be serialised by the caller.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The address is kept for the rest of the process, so the entry
- * point must not be used on a device after cudaDeviceReset (or any other destruction of that
- * device's primary context) in the same process.  Errors: SGSPM_ERR_ARG for bad arguments, SGSPM_ERR_CUDA for a
+ * before any stream capture.  The address is kept with the driver context it was found in and
+ * looked up again when the device's current context is a different one (after
+ * cudaDeviceReset, for example); a call that has to look it up again must also come before
+ * any stream capture.  Errors: SGSPM_ERR_ARG for bad arguments, SGSPM_ERR_CUDA for a
  * failed CUDA call; the text is returned by sgspm_noalloc_last_error (per host thread).
  */
 int sgspm_energy_noalloc(const sgspm_grid* grid, double eps, double Q, const double easy_axis[3],

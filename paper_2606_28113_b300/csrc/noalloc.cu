@@ -28,10 +28,31 @@ constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[4 * kNoallocMaxBlocks];
 
-// Address of g_noalloc_partials on each device, looked up once per device and kept for the rest
-// of the process (valid while that device's primary context lives: not across cudaDeviceReset).
+// Address of g_noalloc_partials on each device, looked up once per device context: the address
+// belongs to the module loaded in that context, so it is looked up again when the device's
+// current context differs from the one it was found in (after cudaDeviceReset, say).
 static double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+static void* g_noalloc_ctx[kNoallocMaxDevices] = {};
 static std::mutex g_noalloc_mu;
+
+// the calling thread's current driver context (through the runtime's driver entry point, so that
+// the library needs no link to the driver library), or nullptr if it cannot be queried
+static void* noalloc_current_context() {
+    typedef int (*CtxGetCurrent)(void**);
+    static CtxGetCurrent fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrent)f;
+    }
+    void* c = nullptr;
+    if (!fn || fn(&c) != 0) return nullptr;
+    return c;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) energy_noalloc_partial_kernel(const T* __restrict__ m, const T* __restrict__ hs,
@@ -103,14 +124,16 @@ static double* noalloc_scratch(std::string* err) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    void* ctx = g_noalloc_ptr[dev] ? noalloc_current_context() : nullptr;
+    if (!g_noalloc_ptr[dev] || !ctx || ctx != g_noalloc_ctx[dev]) {
         double* p = nullptr;
-        e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+        e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);   // makes the device's context current
         if (e != cudaSuccess || !p) {
             *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return nullptr;
         }
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = noalloc_current_context();
     }
     return g_noalloc_ptr[dev];
 }
