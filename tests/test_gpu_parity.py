@@ -41,6 +41,17 @@ def test_fp64_film32x32x4_200_steps_within_rounding_amplification():
     assert np.abs(got - ref).max() <= 10 * sens
 
 
+@pytest.mark.xfail(strict=True, reason="unmet target: 8.6e-11 after 200 steps; the oracle itself moves 5e-11 "
+                                       "under a 1-ulp change of its input, so no FP64 implementation that rounds "
+                                       "differently reaches 1e-12 on this texture")
+def test_fp64_film32x32x4_200_steps_at_the_1e12_target():
+    # the 200-step run of the 32x32x4 film held to the stated FP64 target itself
+    m0 = inputs.random_unit(0, C1["n"])
+    ref, _ = oracle_run(m0, steps=200, **C1)
+    got = gpu_run(m0, 200, **C1)
+    assert np.abs(got - ref).max() <= 1e-12
+
+
 @pytest.mark.parametrize("n", [(12, 10, 3), (24, 20, 1), (40, 1, 1), (6, 15, 5), (96, 8, 2), (5, 4, 2), (1, 9, 4)])
 def test_fp64_ragged_sizes_match_oracle(n):
     # sizes with factors 3 and 5, odd and size-1 axes, and tiles with ragged tails
