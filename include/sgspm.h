@@ -142,7 +142,10 @@ int sgspm_autotune(sgspm_t h, int steps, int* rows_out, int cap);
  * next; the kernels read it at run time, so captured steps pick it up.  ERR_ARG otherwise. */
 int sgspm_set_alpha(sgspm_t h, const double* alpha);
 
-/* Copy a field in (SGSPM_M, SGSPM_HE).  ptr: host or device, layout as above, dtype F32/F64. */
+/* Copy a field in (SGSPM_M, SGSPM_HE).  ptr: host or device, layout as above, dtype F32/F64.
+ * The caller's buffer is read completely before the call returns (it may be reused at once).
+ * SGSPM_M: m is normalised on the device; a zero-length or non-finite vector returns ERR_ARG (the
+ * call waits for that check); the forward transform of the new m is then enqueued on the stream. */
 int sgspm_set_field(sgspm_t h, int which, const void* ptr, int dtype);
 
 /* Copy a field out (SGSPM_M, SGSPM_HS) into host or device memory; synchronises. */

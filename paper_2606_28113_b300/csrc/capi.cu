@@ -1641,6 +1641,9 @@ static int set_field_t(sgspm_t ctx, int which, const void* ptr, int dtype) {
         rc = run_prog(ctx, ctx->fwd_prog, ctx->stream);
         if (rc) return rc;
         ctx->have_m = true;
+        // the status check above synchronised after the copy-in: the caller's buffer is no longer
+        // read, and the forward transform stays ordered on the stream
+        return SGSPM_OK;
     } else {
         if (!ctx->d_he) CK(cudaMalloc(&ctx->d_he, (size_t)3 * n * sizeof(T)));
         he_interleave_kernel<T><<<nb, 256, 0, ctx->stream>>>((T*)ctx->d_he, d0, d1, d2, n);
