@@ -143,12 +143,18 @@ int sgspm_autotune(sgspm_t h, int steps, int* rows_out, int cap);
 int sgspm_set_alpha(sgspm_t h, const double* alpha);
 
 /* Copy a field in (SGSPM_M, SGSPM_HE).  ptr: host or device, layout as above, dtype F32/F64.
+ * Device memory of the current device and page-locked host memory (cudaHostAlloc, or registered
+ * and mapped) are read in place by the copy kernel; pageable and managed memory are first copied
+ * to a device staging buffer on the handle's stream.  Either way the work is ordered on the
+ * handle's stream only: a device buffer written on another stream must be complete first.
  * The caller's buffer is read completely before the call returns (it may be reused at once).
  * SGSPM_M: m is normalised on the device; a zero-length or non-finite vector returns ERR_ARG (the
  * call waits for that check); the forward transform of the new m is then enqueued on the stream. */
 int sgspm_set_field(sgspm_t h, int which, const void* ptr, int dtype);
 
-/* Copy a field out (SGSPM_M, SGSPM_HS) into host or device memory; synchronises. */
+/* Copy a field out (SGSPM_M, SGSPM_HS) into host or device memory; synchronises.  Device memory
+ * of the current device and page-locked host memory are written in place by the copy kernel,
+ * pageable and managed memory through the staging buffer; the result is the same. */
 int sgspm_get_field(sgspm_t h, int which, void* ptr, int dtype);
 
 /* Enqueue n >= 1 time steps on the handle's stream (asynchronous). */

@@ -1605,11 +1605,32 @@ static int check_status(sgspm_ctx* ctx) {
 // ---------------------------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------------------------
+// The address at which the copy kernels can use the caller's buffer in place, or nullptr: device
+// memory of the current device, or page-locked host memory mapped into the device's address space
+// (the kernel's own loads and stores cross the bus, with far more requests in flight than one
+// copy-engine transfer).  Pageable and managed memory go through the staging buffer.
+static const void* direct_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (a.type == cudaMemoryTypeDevice && a.device == dev) return a.devicePointer;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
 template <typename T>
 static int set_field_t(sgspm_t ctx, int which, const void* ptr, int dtype) {
     const long long n = ctx->ncell;
     const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
-    CK(cudaMemcpyAsync(ctx->d_stage, ptr, bytes, cudaMemcpyDefault, ctx->stream));
+    const void* src = direct_ptr(ptr);
+    if (!src) {
+        CK(cudaMemcpyAsync(ctx->d_stage, ptr, bytes, cudaMemcpyDefault, ctx->stream));
+        src = ctx->d_stage;
+    }
     const unsigned nb = (unsigned)((n + 255) / 256);
     T *d0, *d1, *d2, *l0 = nullptr, *l1 = nullptr, *l2 = nullptr;
     if (which == SGSPM_M) {
@@ -1626,10 +1647,10 @@ static int set_field_t(sgspm_t ctx, int which, const void* ptr, int dtype) {
         d2 = (T*)ctx->d_field[HS3];
     }
     if (dtype == SGSPM_F64_DATA)
-        copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const double*)ctx->d_stage,
+        copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const double*)src,
                                                                ctx->d_films, ctx->nfilm, n);
     else
-        copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const float*)ctx->d_stage,
+        copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const float*)src,
                                                               ctx->d_films, ctx->nfilm, n);
     CK(cudaGetLastError());
     if (which == SGSPM_M) {
@@ -1677,15 +1698,19 @@ static int get_field_t(sgspm_t ctx, int which, void* ptr, int dtype) {
     const T* q0 = (const T*)ctx->d_flo[base];
     const T* q1 = (const T*)ctx->d_flo[base + 1];
     const T* q2 = (const T*)ctx->d_flo[base + 2];
+    void* dst = const_cast<void*>(direct_ptr(ptr));
+    void* out = dst ? dst : ctx->d_stage;
     if (dtype == SGSPM_F64_DATA)
-        copy_out_kernel<T, double><<<nb, 256, 0, ctx->stream>>>((double*)ctx->d_stage, s0, s1, s2, q0, q1, q2, ctx->d_films,
+        copy_out_kernel<T, double><<<nb, 256, 0, ctx->stream>>>((double*)out, s0, s1, s2, q0, q1, q2, ctx->d_films,
                                                                 ctx->nfilm, n);
     else
-        copy_out_kernel<T, float><<<nb, 256, 0, ctx->stream>>>((float*)ctx->d_stage, s0, s1, s2, q0, q1, q2, ctx->d_films,
+        copy_out_kernel<T, float><<<nb, 256, 0, ctx->stream>>>((float*)out, s0, s1, s2, q0, q1, q2, ctx->d_films,
                                                                ctx->nfilm, n);
     CK(cudaGetLastError());
-    const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
-    CK(cudaMemcpyAsync(ptr, ctx->d_stage, bytes, cudaMemcpyDefault, ctx->stream));
+    if (!dst) {
+        const size_t bytes = (size_t)3 * n * (dtype == SGSPM_F64_DATA ? 8 : 4);
+        CK(cudaMemcpyAsync(ptr, ctx->d_stage, bytes, cudaMemcpyDefault, ctx->stream));
+    }
     return check_status(ctx);
 }
 

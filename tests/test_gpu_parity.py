@@ -209,3 +209,38 @@ def test_fp32_batch_with_misaligned_film_matches_oracle():
     for f, m0, got in zip(films, m0s, gots):
         ref, _ = oracle_run(m0, steps=6, **f)
         assert np.abs(got - ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_host_pinned_and_device_buffers_give_the_pageable_results(fp64):
+    # set_field / get_field read and write page-locked host and device buffers in place (the
+    # copy kernels' own loads and stores) and pageable ones through a staging copy: every route
+    # must give the same bits, per-film offsets of an uneven batch included
+    import torch
+    films = [dict(n=(16, 8, 2), h=(1 / 16,) * 3, eps=0.016, Q=6.2e-4, alpha=0.02, dt=0.01, he=(0.03, 0, 0)),
+             dict(n=(5, 3, 1), h=(0.2,) * 3, eps=0.016, Q=0.01, alpha=0.05, dt=0.01, he=(0.0, 0.01, 0))]
+    m0 = np.concatenate([inputs.random_unit(60 + i, f["n"]).reshape(-1) for i, f in enumerate(films)])
+    H = sgspm.Handle(films, fp64=fp64)
+    ref = {}
+    for dt in (np.float64, np.float32):
+        H.set_m(m0.astype(dt))
+        H.step(3)
+        ref[dt] = H.get_m()
+    tdt = {np.float64: torch.float64, np.float32: torch.float32}
+    for dt in (np.float64, np.float32):
+        src = torch.from_numpy(m0.astype(dt))
+        for buf in (src.pin_memory(), src.cuda()):
+            H.set_m(buf)
+            H.step(3)
+            for out in (torch.empty(m0.size, dtype=torch.float64).pin_memory(),
+                        torch.empty(m0.size, dtype=torch.float64, device="cuda")):
+                assert np.array_equal(H.get_m(out).cpu().numpy(), ref[dt])
+            o32 = H.get_m(torch.empty(m0.size, dtype=torch.float32).pin_memory()).numpy()
+            assert np.array_equal(o32, H.get_m(np.empty(m0.size, dtype=np.float32)))
+            assert np.array_equal(H.get_m(), ref[dt])
+    bad = torch.from_numpy(m0.copy())
+    bad[7] = float("nan")
+    with pytest.raises(sgspm.SGSPMError) as e:
+        H.set_m(bad.pin_memory())
+    assert e.value.code == sgspm.ERR_ARG
+    H.close()
