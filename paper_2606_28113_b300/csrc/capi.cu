@@ -1433,6 +1433,13 @@ static int setup_t(sgspm_ctx* ctx) {
     CK(ys_attr<T>(std::max(ctx->smem_ys[1], std::max(ctx->smem_ys[2], ctx->smem_ys[3]))));
     // work lists: slab and heat passes per size class (films of one x / y length share a launch)
     std::vector<int4> we;
+    // pointwise and reduction kernels (energy, adjoint): one kThreads CTA per item of `ecell`
+    // cells; 1024 (four cells per thread) where that still gives every SM four CTAs, smaller
+    // items on small grids, which 1024-cell items would leave on a fraction of the SMs
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    long long ecell = 4 * kThreads;
+    while (ecell > kThreads && ctx->ncell / ecell < 4LL * nsm) ecell -= kThreads;
     std::vector<int> first_e;
     auto up4 = [&](int4** d, const std::vector<int4>& h) -> int {
         CK(cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(int4)));
@@ -1451,8 +1458,7 @@ static int setup_t(sgspm_ctx* ctx) {
             sxk[kx] = std::max(sxk[kx], xz_smem_bytes<T>(L));
             first_e.push_back((int)we.size());
             long long nc = (long long)F.nx * F.ny * F.nz;
-            // pointwise and reduction kernels (energy, adjoint): items of 1024 cells, 4 per thread
-            for (long long c0 = 0; c0 < nc; c0 += 1024) we.push_back(make_int4(f, (int)c0, (int)std::min(1024LL, nc - c0), 0));
+            for (long long c0 = 0; c0 < nc; c0 += ecell) we.push_back(make_int4(f, (int)c0, (int)std::min(ecell, nc - c0), 0));
         }
         for (auto& kv : wx) {
             sgspm_ctx::KClass c{kv.first, nullptr, (int)kv.second.size(), sxk[kv.first]};
