@@ -89,6 +89,7 @@ struct sgspm_ctx {
     void* d_he = nullptr;
     bool he_cell = false;
     int* d_status = nullptr;
+    int* h_status = nullptr;   // page-locked host copy of d_status (read by check_status)
     int* d_tc_test = nullptr;          // tensor-core wait test switches (TF32X3 form; see sgspm_test_tc_timeout)
     long long* d_step = nullptr;
     void* d_stage = nullptr;
@@ -1557,6 +1558,7 @@ static int setup_t(sgspm_ctx* ctx) {
     }
     CK(cudaMalloc(&ctx->d_stage, (size_t)3 * ctx->ncell * sizeof(double)));
     CK(cudaMalloc(&ctx->d_status, sizeof(int)));
+    CK(cudaHostAlloc(&ctx->h_status, sizeof(int), cudaHostAllocDefault));
     if (ctx->tf32x3) {
         CK(cudaMalloc(&ctx->d_tc_test, 2 * sizeof(int)));
         CK(cudaMemset(ctx->d_tc_test, 0, 2 * sizeof(int)));
@@ -1595,12 +1597,13 @@ static void release(sgspm_ctx* ctx) {
         for (auto& c : *v)
             if (c.work) cudaFree(c.work);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
 }
 
 static int check_status(sgspm_ctx* ctx) {
-    int st = 0;
-    CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    const int st = *ctx->h_status;
     if (st & 1) return fail(ctx, SGSPM_ERR_NONFINITE, "non-finite value or zero vector before projection");
     if (st & 2) return fail(ctx, SGSPM_ERR_NONFINITE, "set_field: zero-length or non-finite magnetisation vector");
     if (st & 4) return fail(ctx, SGSPM_ERR_TIMEOUT, "a tensor-core transform of the slab pass did not complete in time");
@@ -1652,17 +1655,17 @@ static int set_field_t(sgspm_t ctx, int which, const void* ptr, int dtype) {
         d1 = (T*)ctx->d_field[HS2];
         d2 = (T*)ctx->d_field[HS3];
     }
+    // m is normalised by the copy kernel itself (status: bit 2 for a zero-length or non-finite vector)
+    int* status = which == SGSPM_M ? ctx->d_status : nullptr;
+    if (status) CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
     if (dtype == SGSPM_F64_DATA)
         copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const double*)src,
-                                                               ctx->d_films, ctx->nfilm, n);
+                                                               ctx->d_films, ctx->nfilm, n, status);
     else
         copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, (const float*)src,
-                                                              ctx->d_films, ctx->nfilm, n);
+                                                              ctx->d_films, ctx->nfilm, n, status);
     CK(cudaGetLastError());
     if (which == SGSPM_M) {
-        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-        normalize_kernel<T><<<nb, 256, 0, ctx->stream>>>(d0, d1, d2, l0, l1, l2, n, ctx->d_status);
-        CK(cudaGetLastError());
         int rc = check_status(ctx);
         if (rc) return fail(ctx, SGSPM_ERR_ARG, "set_field: zero-length or non-finite magnetisation vector");
         rc = run_prog(ctx, ctx->fwd_prog, ctx->stream);
@@ -1807,10 +1810,12 @@ static int grad_t(sgspm_ctx* ctx, const void* dL_dmT, int dtype, void* dL_dhe, d
     T* g2 = (T*)ctx->d_field[G3];
     if (dtype == SGSPM_F64_DATA)
         copy_in_kernel<T, double><<<nb, 256, 0, ctx->stream>>>(g0, g1, g2, nullptr, nullptr, nullptr,
-                                                               (const double*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+                                                               (const double*)ctx->d_stage, ctx->d_films, ctx->nfilm, n,
+                                                               nullptr);
     else
         copy_in_kernel<T, float><<<nb, 256, 0, ctx->stream>>>(g0, g1, g2, nullptr, nullptr, nullptr,
-                                                              (const float*)ctx->d_stage, ctx->d_films, ctx->nfilm, n);
+                                                              (const float*)ctx->d_stage, ctx->d_films, ctx->nfilm, n,
+                                                              nullptr);
     CK(cudaGetLastError());
     if ((rc = state_io<T>(ctx, (T*)ctx->d_final, true))) return rc;
     for (int a = 0; a < 3; ++a) CK(cudaMemsetAsync(ctx->d_field[bHE1 + a], 0, (size_t)n * sizeof(T), ctx->stream));

@@ -82,8 +82,9 @@ __global__ void energy_final_kernel(const Film* films, int nfilm, const int* __r
 template <typename T, typename S>
 __global__ void copy_in_kernel(T* __restrict__ d0, T* __restrict__ d1, T* __restrict__ d2, T* __restrict__ l0,
                                T* __restrict__ l1, T* __restrict__ l2, const S* __restrict__ src,
-                               const Film* films, int nfilm, long long ntot) {
-    // src: concatenation over films of [3][ncell_f]
+                               const Film* films, int nfilm, long long ntot, int* status) {
+    // src: concatenation over films of [3][ncell_f]; with status non-null (magnetisation) the
+    // stored vector (hi + lo) is normalised, and a zero-length or non-finite one sets bit 2
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= ntot) return;
     int f = 0;
@@ -94,10 +95,27 @@ __global__ void copy_in_kernel(T* __restrict__ d0, T* __restrict__ d1, T* __rest
     const S* s = src + 3 * F.off_cell;
     T* dd[3] = {d0, d1, d2};
     T* ll[3] = {l0, l1, l2};
+    double v[3];
     for (int a = 0; a < 3; ++a) {
-        const double v = (double)s[a * nc + loc];
-        dd[a][i] = (T)v;
-        if (ll[a]) ll[a][i] = (T)(v - (double)(T)v);
+        const double x = (double)s[a * nc + loc];
+        const T hi = (T)x, lo = (T)(x - (double)hi);
+        v[a] = (double)hi + (ll[a] ? (double)lo : 0.0);
+        if (!status) {
+            dd[a][i] = hi;
+            if (ll[a]) ll[a][i] = lo;
+        }
+    }
+    if (!status) return;
+    const double n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    if (!(n2 > 0.0) || !isfinite(n2)) {
+        atomicOr(status, 2);
+        return;
+    }
+    const double inv = 1.0 / sqrt(n2);
+    for (int a = 0; a < 3; ++a) {
+        const double w = v[a] * inv;
+        dd[a][i] = (T)w;
+        if (ll[a]) ll[a][i] = (T)(w - (double)(T)w);
     }
 }
 
@@ -116,27 +134,6 @@ __global__ void copy_out_kernel(S* __restrict__ dst, const T* __restrict__ d0, c
     const T* dd[3] = {d0, d1, d2};
     const T* ll[3] = {l0, l1, l2};
     for (int a = 0; a < 3; ++a) s[a * nc + loc] = (S)((double)dd[a][i] + (ll[a] ? (double)ll[a][i] : 0.0));
-}
-
-template <typename T>
-__global__ void normalize_kernel(T* m0, T* m1, T* m2, T* l0, T* l1, T* l2, long long n, int* status) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T* mm[3] = {m0, m1, m2};
-    T* ll[3] = {l0, l1, l2};
-    double v[3];
-    for (int a = 0; a < 3; ++a) v[a] = (double)mm[a][i] + (ll[a] ? (double)ll[a][i] : 0.0);
-    double n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    if (!(n2 > 0.0) || !isfinite(n2)) {
-        atomicOr(status, 2);
-        return;
-    }
-    double inv = 1.0 / sqrt(n2);
-    for (int a = 0; a < 3; ++a) {
-        double w = v[a] * inv;
-        mm[a][i] = (T)w;
-        if (ll[a]) ll[a][i] = (T)(w - (double)(T)w);
-    }
 }
 
 template <typename T>
