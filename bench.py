@@ -195,7 +195,8 @@ def algorithmic_bytes_per_cell(kind, ncomp=1):
 
 def run_ensemble(sgspm, torch, stream, steps, warmup=3):
     """Aggregate throughput of the batched workload: 256 films of four sizes in one handle (FP32),
-    each step one persistent launch over all films; the per-pass launches (24 per step) beside it."""
+    stepped by per-pass launches (24 per step, CUDA graph) and by one persistent launch per step;
+    the line reports the faster form, the other beside it."""
     films = inputs.ensemble(seed=0, nfilm=256)
     m0 = np.concatenate([inputs.random_unit(f["seed"], f["n"]).reshape(-1) for f in films])
     ncell = sum(int(np.prod(f["n"])) for f in films)
@@ -221,7 +222,9 @@ def run_ensemble(sgspm, torch, stream, steps, warmup=3):
         ms = timed()
         r = {"ms_per_step": ms / steps, "value": ncell * steps / (ms / 1e3), "unit": UNIT,
              "launches_per_step": H.launches_per_step(), "ms_per_step_untuned": ms_untuned / steps,
-             "autotuned_packing": {f"nx class {k}": p for (k, _), p in zip(H.xz_classes(), packing)}}
+             "autotuned_packing": {f"nx class {k}": p for (k, _), p in zip(H.xz_classes(), packing)},
+             "autotuned_packed_threads": {f"nx class {k}": t for (k, p), t in zip(H.xz_classes(), H.packing_threads())
+                                          if p > 1}}
         if not persistent:
             prof = {}
             for kind, t in H.profile_step():
@@ -241,6 +244,7 @@ def run_ensemble(sgspm, torch, stream, steps, warmup=3):
             "form": names[best], "value": head["value"], "unit": UNIT, "ms_per_step": head["ms_per_step"],
             "steps": steps, "warmup": warmup, "dtype": "f32", "l2": "working set larger than L2 (no flush)",
             "launches_per_step": head["launches_per_step"], "autotuned_packing": head["autotuned_packing"],
+            "autotuned_packed_threads": head["autotuned_packed_threads"],
             "ms_per_step_untuned": head["ms_per_step_untuned"], "launch_shares": res["per_pass"].get("launch_shares"),
             "other_form": dict(res[other], form=names[other])}
 

@@ -100,6 +100,7 @@ struct sgspm_ctx {
         int n;
         size_t smem;
         int rows = 1;                  // slab pass: y rows per CTA (batch packing)
+        int threads = kThreads;        // slab pass: threads per packed CTA (below kThreads: packed even at one row)
         bool nz8 = true;               // slab pass: every film of the class has nz = kZReg
     };
     std::vector<KClass> xz_cls, yh_cls, yw_cls;
@@ -278,17 +279,18 @@ static void launch_xz_mode(int mode, int nb, size_t smem, cudaStream_t st, const
 
 template <typename T>
 static void launch_xz(int key, int nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray,
-                      bool tf32x3, int rows, bool nz8) {
+                      bool tf32x3, int rows, bool nz8, int threads) {
     if constexpr (sizeof(T) == 8) {   // the FP64 form uses the runtime-length kernel only
         xz_go<T, 0, false, false>(nb, smem, st, d, w, pg, stray);
         return;
     } else {
-        if (rows > 1) {
+        // the packed-row kernel: several rows per CTA, or one row with fewer threads than kThreads
+        if (rows > 1 || threads < kThreads) {
             switch (key) {
-                case 64: xz_go<T, 64, false, true>(nb, smem, st, d, w, pg, stray); return;
-                case 128: xz_go<T, 128, false, true>(nb, smem, st, d, w, pg, stray); return;
-                case 256: xz_go<T, 256, false, true>(nb, smem, st, d, w, pg, stray); return;
-                default: xz_go<T, 0, false, true>(nb, smem, st, d, w, pg, stray); return;
+                case 64: xz_go<T, 64, false, true>(nb, smem, st, d, w, pg, stray, threads); return;
+                case 128: xz_go<T, 128, false, true>(nb, smem, st, d, w, pg, stray, threads); return;
+                case 256: xz_go<T, 256, false, true>(nb, smem, st, d, w, pg, stray, threads); return;
+                default: xz_go<T, 0, false, true>(nb, smem, st, d, w, pg, stray, threads); return;
             }
         }
         if (ztc_class(tf32x3, key)) {
@@ -428,7 +430,7 @@ static int enqueue_t(sgspm_ctx* ctx, const Launch& L, cudaStream_t st) {
     switch (L.kind) {
         case 0:
             for (const auto& c : ctx->xz_cls)
-                launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3, c.rows, c.nz8);
+                launch_xz<T>(c.key, c.n, c.smem, st, d, c.work, L.xz, ctx->stray ? 1 : 0, ctx->tf32x3, c.rows, c.nz8, c.threads);
             break;
         case 1:
             for (const auto& c : ctx->yh_cls) launch_yh<T>(c.key, c.n, c.smem, st, d, c.work, L.y, ctx->heat_threads);
@@ -2027,8 +2029,13 @@ int sgspm_step(sgspm_t ctx, long long n) {
 static int xz_class_key(const sgspm_ctx* ctx, const Film& F) { return xz_key(ctx->fp64, F); }
 
 // Rebuild the slab-pass work list of class c with `rows` y rows per CTA.
-static int set_class_rows(sgspm_ctx* ctx, size_t c, int rows) {
+static int set_class_rows(sgspm_ctx* ctx, size_t c, int rows, int threads) {
     auto& K = ctx->xz_cls[c];
+    if (K.rows == rows && K.work) {
+        if (K.threads != threads) drop_graph(ctx);
+        K.threads = threads;
+        return SGSPM_OK;
+    }
     std::vector<int4> w;
     for (int f = 0; f < ctx->nfilm; ++f) {
         const Film& F = ctx->films[f];
@@ -2043,6 +2050,7 @@ static int set_class_rows(sgspm_ctx* ctx, size_t c, int rows) {
     K.work = d;
     K.n = (int)w.size();
     K.rows = rows;
+    K.threads = threads;
     drop_graph(ctx);
     return SGSPM_OK;
 }
@@ -2080,9 +2088,33 @@ int sgspm_set_packing(sgspm_t ctx, const int* rows, int n) {
     }
     for (int c = 0; c < n; ++c)
         if (rows[c] != ctx->xz_cls[c].rows) {
-            int rc = set_class_rows(ctx, (size_t)c, rows[c]);
+            int rc = set_class_rows(ctx, (size_t)c, rows[c], ctx->xz_cls[c].threads);
             if (rc) return rc;
         }
+    return SGSPM_OK;
+}
+
+int sgspm_xz_threads(sgspm_t ctx, int* threads, int cap) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    const int n = (int)ctx->xz_cls.size();
+    if (threads && cap < n) return fail(ctx, SGSPM_ERR_ARG, "cap is below the number of size classes");
+    for (int c = 0; threads && c < n; ++c) threads[c] = ctx->xz_cls[c].threads;
+    return n;
+}
+
+int sgspm_set_packing_threads(sgspm_t ctx, const int* threads, int n) {
+    if (!ctx) return SGSPM_ERR_ARG;
+    if (!threads || n != (int)ctx->xz_cls.size()) return fail(ctx, SGSPM_ERR_ARG, "threads must have one entry per size class");
+    for (int c = 0; c < n; ++c) {
+        if (threads[c] != 64 && threads[c] != 128 && threads[c] != kThreads)
+            return fail(ctx, SGSPM_ERR_ARG, "threads per packed CTA must be 64, 128 or 256");
+        if (threads[c] != kThreads && !packable_class(ctx->fp64, ctx->tf32x3, ctx->xz_cls[c].key))
+            return fail(ctx, SGSPM_ERR_UNSUPPORTED, "this size class runs its own kernels only");
+    }
+    for (int c = 0; c < n; ++c) {
+        int rc = set_class_rows(ctx, (size_t)c, ctx->xz_cls[c].rows, threads[c]);
+        if (rc) return rc;
+    }
     return SGSPM_OK;
 }
 
@@ -2124,9 +2156,13 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
         for (const Film& F : ctx->films)
             if (xz_class_key(ctx, F) == ctx->xz_cls[c].key) maxny = std::max(maxny, F.ny);
         float best = 1e30f;
-        int best_rows = 1;
-        for (int r = 1; r <= kMaxRowsPerCTA && r <= maxny && !rc; r *= 2) {
-            if ((rc = set_class_rows(ctx, (size_t)c, r))) break;
+        int best_rows = 1, best_th = kThreads;
+        // 1, 2, 4, 8 rows per CTA with 256, 128 or 64 threads (one row with 256: the class's own
+        // kernels)
+        for (int cand = 0; cand < 12 && !rc; ++cand) {
+            const int r = 1 << (cand / 3), th = kThreads >> (cand % 3);
+            if (r > kMaxRowsPerCTA || r > maxny) continue;
+            if ((rc = set_class_rows(ctx, (size_t)c, r, th))) break;
             if ((rc = sgspm_step(ctx, 1))) break;   // captures the graph of this packing
             if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = SGSPM_ERR_CUDA; break; }
             if ((rc = sgspm_step(ctx, steps))) break;
@@ -2139,9 +2175,10 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
             if (ms < best) {
                 best = ms;
                 best_rows = r;
+                best_th = th;
             }
         }
-        if (!rc) rc = set_class_rows(ctx, (size_t)c, best_rows);
+        if (!rc) rc = set_class_rows(ctx, (size_t)c, best_rows, best_th);
     }
     // y heat pass: x lines per CTA
     if (!rc) {

@@ -7,8 +7,10 @@
 namespace sgspm {
 
 template <typename T, int NX, bool ZTC, bool MULTI, int MODE>
-void xz_go(unsigned nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray) {
-    launch_pdl(xz_kernel<T, NX, ZTC, MULTI, MODE>, nb, xz_nt<NX, MODE, MULTI, ZTC>(), smem, st, d, w, pg, stray);
+void xz_go(unsigned nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray,
+           unsigned nt) {
+    launch_pdl(xz_kernel<T, NX, ZTC, MULTI, MODE>, nb, nt ? nt : (unsigned)xz_nt<NX, MODE, MULTI, ZTC>(), smem, st, d, w, pg,
+               stray);
 }
 template <typename T, int NX, bool ZTC, bool MULTI, int MODE>
 cudaError_t xz_attr(size_t smem) {
@@ -53,20 +55,20 @@ cudaError_t ys_attr(size_t smem) {
 // explicit instantiation of one variant of each family
 #define SGSPM_INST_XZ(T, NX, ZTC, MULTI)                                                                        \
     template void sgspm::xz_go<T, NX, ZTC, MULTI, 0>(unsigned, size_t, cudaStream_t, const sgspm::Dev<T>&,     \
-                                                     const int4*, const sgspm::XZProg&, int);                   \
+                                                     const int4*, const sgspm::XZProg&, int, unsigned);         \
     template cudaError_t sgspm::xz_attr<T, NX, ZTC, MULTI, 0>(size_t);                                          \
     template long long sgspm::xz_static_smem<T, NX, ZTC, MULTI>();
 // the three launch-type specialisations of one single-row FP32 size class
 #define SGSPM_INST_XZ_MODES(NX)                                                                                  \
     template void sgspm::xz_go<float, NX, false, false, 1>(unsigned, size_t, cudaStream_t,                     \
                                                            const sgspm::Dev<float>&, const int4*,               \
-                                                           const sgspm::XZProg&, int);                          \
+                                                           const sgspm::XZProg&, int, unsigned);                \
     template void sgspm::xz_go<float, NX, false, false, 2>(unsigned, size_t, cudaStream_t,                     \
                                                            const sgspm::Dev<float>&, const int4*,               \
-                                                           const sgspm::XZProg&, int);                          \
+                                                           const sgspm::XZProg&, int, unsigned);                \
     template void sgspm::xz_go<float, NX, false, false, 3>(unsigned, size_t, cudaStream_t,                     \
                                                            const sgspm::Dev<float>&, const int4*,               \
-                                                           const sgspm::XZProg&, int);                          \
+                                                           const sgspm::XZProg&, int, unsigned);                \
     template cudaError_t sgspm::xz_attr<float, NX, false, false, 1>(size_t);                                    \
     template cudaError_t sgspm::xz_attr<float, NX, false, false, 2>(size_t);                                    \
     template cudaError_t sgspm::xz_attr<float, NX, false, false, 3>(size_t);

@@ -52,6 +52,8 @@ def lib():
     ip = ctypes.POINTER(ctypes.c_int)
     L.sgspm_xz_classes.argtypes = [vp, ip, ip, i]
     L.sgspm_set_packing.argtypes = [vp, ip, i]
+    L.sgspm_xz_threads.argtypes = [vp, ip, i]
+    L.sgspm_set_packing_threads.argtypes = [vp, ip, i]
     L.sgspm_autotune.argtypes = [vp, i, ip, i]
     L.sgspm_heat_tile.argtypes = [vp]
     L.sgspm_set_heat_tile.argtypes = [vp, i]
@@ -80,7 +82,8 @@ def lib():
     L.sgspm_energy_noalloc.restype = ctypes.c_int
     L.sgspm_noalloc_last_error.argtypes = []
     L.sgspm_noalloc_last_error.restype = ctypes.c_char_p
-    for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_alpha", "sgspm_xz_classes", "sgspm_set_packing", "sgspm_autotune",
+    for name in ("sgspm_create", "sgspm_create_batch", "sgspm_set_applied_field", "sgspm_set_alpha", "sgspm_xz_classes", "sgspm_set_packing", "sgspm_xz_threads",
+                 "sgspm_set_packing_threads", "sgspm_autotune",
                  "sgspm_heat_tile", "sgspm_set_heat_tile",
                  "sgspm_set_field",
                  "sgspm_get_field", "sgspm_step", "sgspm_energy", "sgspm_set_forcing", "sgspm_set_time",
@@ -226,6 +229,17 @@ class Handle:
         r = (ctypes.c_int * len(rows))(*[int(v) for v in rows])
         self._check(lib().sgspm_set_packing(self.h, r, len(rows)))
 
+    def packing_threads(self):
+        """Threads per CTA of each size class's packed (rows > 1) slab launches."""
+        n = len(self.xz_classes())
+        t = (ctypes.c_int * max(n, 1))()
+        self._check(min(0, lib().sgspm_xz_threads(self.h, t, n)))
+        return [t[c] for c in range(n)]
+
+    def set_packing_threads(self, threads):
+        t = (ctypes.c_int * len(threads))(*[int(v) for v in threads])
+        self._check(lib().sgspm_set_packing_threads(self.h, t, len(threads)))
+
     def heat_tile(self):
         """x lines per CTA of the y heat pass."""
         rc = lib().sgspm_heat_tile(self.h)
@@ -237,7 +251,7 @@ class Handle:
         self._check(lib().sgspm_set_heat_tile(self.h, int(tx)))
 
     def autotune(self, steps=3):
-        """Choose rows per CTA of every packable size class by timing; returns the choice."""
+        """Choose rows (and threads) per CTA of every packable size class by timing; returns the rows."""
         n = len(self.xz_classes())
         out = (ctypes.c_int * max(n, 1))()
         rc = lib().sgspm_autotune(self.h, int(steps), out, n)

@@ -68,6 +68,8 @@ def test_null_handle_tuning_and_parameter_calls_are_rejected():
     assert L.sgspm_set_alpha(None, a) == sgspm.ERR_ARG
     assert L.sgspm_xz_classes(None, None, None, 0) == sgspm.ERR_ARG
     assert L.sgspm_set_packing(None, r, 1) == sgspm.ERR_ARG
+    assert L.sgspm_xz_threads(None, None, 0) == sgspm.ERR_ARG
+    assert L.sgspm_set_packing_threads(None, r, 1) == sgspm.ERR_ARG
     assert L.sgspm_autotune(None, 1, None, 0) == sgspm.ERR_ARG
     assert L.sgspm_heat_tile(None) == sgspm.ERR_ARG
     assert L.sgspm_set_heat_tile(None, 6) == sgspm.ERR_ARG
