@@ -1060,9 +1060,8 @@ static int build_persist(sgspm_ctx* ctx) {
             } else if (L.kind == 1) {
                 const int key = pow2_key(F.ny, 8, 512);
                 const int pkey = (key == 64 || key == 128 || key == 256) ? key : 0;
-                // about 2048 cells per item (at least the tuned tile): short lines get wide tiles,
-                // since the persistent kernel keeps only two CTAs per multiprocessor
-                const int tx = std::max(ctx->tx_h, std::min(32, std::max(1, 2048 / F.ny)));
+                // about 8 cells per thread (at least the tuned tile): short lines get wide tiles
+                const int tx = std::max(ctx->tx_h, std::min(32, std::max(1, 8 * kPersistThreads / F.ny)));
                 for (int kz = 0; kz < F.nz; ++kz)
                     for (int x0 = 0; x0 < F.nx; x0 += tx, ++nf) add(make_int4(f, kz, x0, std::min(tx, F.nx - x0)), pkey);
                 smem = std::max(smem, heat_smem<float>(F.ny, tx));

@@ -9,7 +9,7 @@ namespace sgspm {
 void persist_go(unsigned grid, size_t smem, cudaStream_t st, const Dev<float>& d, const PersistArgs& a) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kPersistThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -26,7 +26,7 @@ cudaError_t persist_attr(size_t smem) {
 
 int persist_blocks_per_sm(size_t smem) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist_kernel, kThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist_kernel, kPersistThreads, smem) != cudaSuccess) return 0;
     return nb;
 }
 

@@ -105,7 +105,11 @@ __host__ __device__ inline size_t yw_smem_bytes(int Py, int nout, int lines = kW
 // An item of phase q of film f may start once all of film f's items of phases < q are complete: a
 // per-film counter of completed items, waited on with a bounded acquire-spin.  Films never wait on
 // each other, so the tail of one phase of a film overlaps other films' work.
-constexpr int kPersistLines = 8;   // kx lines per stray item (one warp each, kThreads threads)
+// 64-thread CTAs (eight per SM at 128 registers): the slab items of thin films run one warp per x
+// line, so small CTAs leave few warps idle (256-thread CTAs made the 256-film step 16.7 ms, 128
+// 12.4 ms, 64 11.7 ms; 64 with 255 registers 15.1 ms, 32 threads 16.8 ms)
+constexpr int kPersistThreads = 64;   // threads per CTA of the persistent kernel
+constexpr int kPersistLines = kPersistThreads / 32;   // kx lines per stray item (one warp each)
 
 struct PPhase {
     int kind;       // 0 slab pass, 1 heat line pass, 2 stray line pass

@@ -63,7 +63,7 @@ __device__ __forceinline__ void persist_item(const Dev<float>& d, const PPhase& 
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) persist_kernel(const __grid_constant__ Dev<float> d, const __grid_constant__ PersistArgs a) {
+__global__ void __launch_bounds__(kPersistThreads, 512 / kPersistThreads) persist_kernel(const __grid_constant__ Dev<float> d, const __grid_constant__ PersistArgs a) {
     // the current item, decoded by thread 0; the phase program is copied here when it changes
     __shared__ __align__(16) PPhase s_ph;
     __shared__ int4 s_wi;
