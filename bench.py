@@ -49,12 +49,20 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms; summary() keeps the samples read
+    between mark_start() and mark_end() (the timed region)."""
 
     def __init__(self, index):
         self.index = index
         self.rows = []
         self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
 
     def __enter__(self):
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -62,7 +70,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -72,7 +80,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.monotonic(), [x.strip() for x in line.split(",")]))
 
     def __exit__(self, *a):
         if self.proc:
@@ -85,7 +93,11 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        # a row is printed when its sample has been taken: keep rows read in the timed region
+        # and up to one interval after it
+        rows = [r for t, r in self.rows
+                if self.t0 is None or (t >= self.t0 and (self.t1 is None or t <= self.t1 + 0.05))]
+        for r in rows:
             try:
                 sm.append(float(r[0]))
                 smax = float(r[1])
@@ -375,12 +387,20 @@ def run_gpu(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     with ClockSampler(local) as clk:
+        # untimed steps until the sampler reports (at most 3 s), so that it samples the timed region
+        t_wait = time.monotonic()
+        while clk.proc is not None and not clk.rows and time.monotonic() - t_wait < 3.0:
+            H.step(20)
+            H.sync()
+        barrier()
+        clk.mark_start()
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
             H.step(1)
             ev[i][1].record(stream)
         barrier()
+        clk.mark_end()
     step_ms, value = whole_job(sum(a.elapsed_time(b) for a, b in ev), ncell, args.steps, world, "cuda")
     H.sync()
 
