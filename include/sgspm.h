@@ -124,14 +124,14 @@ int sgspm_set_applied_field(sgspm_t h, const double* he);
  *   class that runs one row per CTA.  Results do not depend on the packing (bitwise).
  * sgspm_xz_threads: threads per CTA of each class's packed launches (cap entries when threads is
  *   non-NULL); returns the number of classes.  Default 256.
- * sgspm_set_packing_threads: 64, 128 or 256 threads per packed CTA, one entry per class (ERR_ARG
- *   otherwise; ERR_UNSUPPORTED below 256 on a class that cannot be packed).  A class runs the
+ * sgspm_set_packing_threads: 32, 64, 128 or 256 threads per packed CTA, one entry per class
+ *   (ERR_ARG otherwise; ERR_UNSUPPORTED below 256 on a class that cannot be packed).  A class runs the
  *   packed kernel when it has more than one row per CTA or fewer than 256 threads; one row with
  *   256 runs the class's own kernels.  With fewer threads more CTAs share an SM, and the x
  *   transforms of thin slabs (nz lines per row) leave fewer warps idle.  Results do not depend on
  *   it (bitwise).
  * sgspm_autotune: times `steps` steps of every packable class for 1, 2, 4, 8 rows per CTA with
- *   256, 128 or 64 threads, keeps the fastest, then the heat tile (below) the same way;
+ *   256, 128, 64 or 32 threads, keeps the fastest, then the heat tile (below) the same way;
  *   m and the step count are restored afterwards (it allocates a copy of m while it runs).  Needs
  *   m set (ERR_STATE).  Writes the chosen rows to rows_out (cap entries) when non-NULL and
  *   returns the number of classes.

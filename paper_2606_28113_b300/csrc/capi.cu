@@ -2105,8 +2105,8 @@ int sgspm_set_packing_threads(sgspm_t ctx, const int* threads, int n) {
     if (!ctx) return SGSPM_ERR_ARG;
     if (!threads || n != (int)ctx->xz_cls.size()) return fail(ctx, SGSPM_ERR_ARG, "threads must have one entry per size class");
     for (int c = 0; c < n; ++c) {
-        if (threads[c] != 64 && threads[c] != 128 && threads[c] != kThreads)
-            return fail(ctx, SGSPM_ERR_ARG, "threads per packed CTA must be 64, 128 or 256");
+        if (threads[c] != 32 && threads[c] != 64 && threads[c] != 128 && threads[c] != kThreads)
+            return fail(ctx, SGSPM_ERR_ARG, "threads per packed CTA must be 32, 64, 128 or 256");
         if (threads[c] != kThreads && !packable_class(ctx->fp64, ctx->tf32x3, ctx->xz_cls[c].key))
             return fail(ctx, SGSPM_ERR_UNSUPPORTED, "this size class runs its own kernels only");
     }
@@ -2156,10 +2156,10 @@ int sgspm_autotune(sgspm_t ctx, int steps, int* rows_out, int cap) {
             if (xz_class_key(ctx, F) == ctx->xz_cls[c].key) maxny = std::max(maxny, F.ny);
         float best = 1e30f;
         int best_rows = 1, best_th = kThreads;
-        // 1, 2, 4, 8 rows per CTA with 256, 128 or 64 threads (one row with 256: the class's own
-        // kernels)
-        for (int cand = 0; cand < 12 && !rc; ++cand) {
-            const int r = 1 << (cand / 3), th = kThreads >> (cand % 3);
+        // 1, 2, 4, 8 rows per CTA with 256, 128, 64 or 32 threads (one row with 256: the class's
+        // own kernels)
+        for (int cand = 0; cand < 16 && !rc; ++cand) {
+            const int r = 1 << (cand / 4), th = kThreads >> (cand % 4);
             if (r > kMaxRowsPerCTA || r > maxny) continue;
             if ((rc = set_class_rows(ctx, (size_t)c, r, th))) break;
             if ((rc = sgspm_step(ctx, 1))) break;   // captures the graph of this packing

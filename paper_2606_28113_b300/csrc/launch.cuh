@@ -27,7 +27,7 @@ static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, 
 // XZ slab pass: NX compile-time x length (0: runtime), ZTC tensor-core z transforms, MULTI
 // several y rows per CTA, MODE launch type (0 generic, 1 rhs, 2 Gauss-Seidel, 3 final).
 // nt: threads per CTA (0: the variant's own count, xz_nt); the packed-row (MULTI) variants also run
-// with 64 or 128, since every loop of the slab pass strides by blockDim.x
+// with 32, 64 or 128, since every loop of the slab pass strides by blockDim.x
 template <typename T, int NX, bool ZTC, bool MULTI, int MODE = 0>
 void xz_go(unsigned nb, size_t smem, cudaStream_t st, const Dev<T>& d, const int4* w, const XZProg& pg, int stray,
            unsigned nt = 0);

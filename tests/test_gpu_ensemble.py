@@ -76,7 +76,7 @@ def test_packing_and_autotune_leave_results_unchanged():
     for rows in (2, 4, 8):
         got, _ = run(lambda H: H.set_packing([rows] * len(cls)))
         assert np.array_equal(got, base), rows
-    for rows, th in ((4, 64), (4, 128), (1, 64)):
+    for rows, th in ((4, 64), (4, 128), (1, 64), (2, 32)):
         def packed(H):
             H.set_packing([rows] * len(cls))
             H.set_packing_threads([th] * len(cls))
@@ -112,7 +112,7 @@ def test_tuning_calls_validate_their_arguments():
         H.set_packing([1 if k == 64 else 2 for k, _ in cls])   # the nx 512 class runs one row per CTA
     assert e.value.code == sgspm.ERR_UNSUPPORTED
     with pytest.raises(sgspm.SGSPMError) as e:
-        H.set_packing_threads([96] * len(cls))   # 64, 128 or 256
+        H.set_packing_threads([96] * len(cls))   # 32, 64, 128 or 256
     assert e.value.code == sgspm.ERR_ARG
     with pytest.raises(sgspm.SGSPMError) as e:
         H.set_packing_threads([128])             # one entry per class
