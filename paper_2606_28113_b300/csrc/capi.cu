@@ -132,6 +132,7 @@ struct sgspm_ctx {
     PItem* d_pit = nullptr;
     int* d_pfi = nullptr;
     unsigned* d_pctl = nullptr;        // ticket, abandon flag, per-film completed items
+    bool p_stale = true;               // the persistent item tables predate a packing or program change
     int p_nphase = 0, p_items = 0, p_grid = 0;
     size_t p_smem = 0;
     long long p_wait_limit = 4000000000LL;   // clock cycles (about 2 s at 2 GHz)
@@ -964,6 +965,7 @@ static int drop_graph(sgspm_ctx* ctx) {
     ctx->graph = nullptr;
     ctx->adj_gexec = nullptr;
     ctx->adj_graph = nullptr;
+    ctx->p_stale = true;
     return SGSPM_OK;
 }
 
@@ -1090,6 +1092,7 @@ static int build_persist(sgspm_ctx* ctx) {
     CK(cudaMalloc(&ctx->d_pfi, per_film.size() * sizeof(int)));
     CK(cudaMemcpy(ctx->d_pfi, per_film.data(), per_film.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_pctl, (2 + ctx->nfilm) * sizeof(unsigned)));
+    ctx->p_stale = false;
     CK(persist_attr(smem));
     const int per_sm = persist_blocks_per_sm(smem);
     int dev = 0, nsm = 0;
@@ -2005,7 +2008,7 @@ int sgspm_step(sgspm_t ctx, long long n) {
     if (n < 1) return fail(ctx, SGSPM_ERR_ARG, "n must be >= 1");
     if (!ctx->have_m) return fail(ctx, SGSPM_ERR_STATE, "m has not been set");
     if (ctx->flags & SGSPM_NO_GRAPH) {
-        if (ctx->persist && !ctx->d_pctl) {
+        if (ctx->persist && (ctx->p_stale || !ctx->d_pctl)) {
             int rc = build_persist(ctx);
             if (rc) return rc;
         }
