@@ -58,6 +58,18 @@ def test_persistent_step_is_bitwise_the_per_pass_step():
     assert np.array_equal(packed, base)
     tiled, _ = _run(FILMS, m0, 10, setup=lambda H: H.set_heat_tile(4), persistent=True)
     assert np.array_equal(tiled, base)
+    # without the graph, packing and tile changes between steps rebuild the item tables
+    H = sgspm.Handle(FILMS, persistent=True, graph=False)
+    H.set_m(m0)
+    H.step(3)
+    H.set_packing([2] * len(H.xz_classes()))
+    H.set_packing_threads([64] * len(H.xz_classes()))
+    H.step(4)
+    H.set_heat_tile(6)
+    H.step(3)
+    assert H.xz_classes()[0][1] == 2
+    assert np.array_equal(H.get_m(), base)
+    H.close()
 
 
 def test_persistent_step_rejects_what_it_does_not_run():
