@@ -195,10 +195,13 @@ int sgspm_get_time(sgspm_t h, double* t);
  *
  * sgspm_record: from the current m (= m(0)), advance nsteps >= 1 steps, keeping a checkpoint of
  *   the state every K >= 1 steps in device memory (nsteps/K checkpoints).  Afterwards m = m(T).
+ *   It also reserves, when the device has room, 29 real fields per step of a segment (K x 29 x
+ *   ncell values of the form's precision) for the reverse sweep.
  * sgspm_grad: dL_dmT = dL/dm(T) in the field layout (host or device, dtype SGSPM_F32 or
- *   SGSPM_F64_DATA).  Runs the reverse sweep: each segment is recomputed from its checkpoint and
- *   every step is replayed once more in recording form (storing its intermediates) before the
- *   hand-written reverse of that step.  Writes dL/dh_e (same layout and dtype as dL_dmT; the
+ *   SGSPM_F64_DATA).  Runs the reverse sweep: each segment is recomputed from its checkpoint in
+ *   recording form, keeping every step's intermediates in the reserved fields, and the steps are
+ *   then reversed with the hand-written reverse step; without the reserved fields every step is
+ *   replayed once more in recording form before its reverse (the same results, more time).  Writes dL/dh_e (same layout and dtype as dL_dmT; the
  *   gradient with respect to a per-cell applied field, also when the field is uniform) and
  *   dL/dalpha (nfilm host doubles).  Only the dependence through m(T) is included: a loss term
  *   on h_e or alpha itself is the caller's.  Synchronises; m is m(T) again on return.

@@ -212,6 +212,18 @@ __global__ void adj_alpha_final_kernel(int nfilm, const int* __restrict__ first_
     alpha_b[f] += s;
 }
 
+// The recorded real slots 0 .. nslot-1 (hi parts) of one step <-> buf [nslot][n]; slot pointers
+// from the device slot table; blockIdx.y is the slot
+template <typename T>
+__global__ void slots_io_kernel(T* __restrict__ buf, void* const* __restrict__ tab, long long n, int save) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T* f = static_cast<T*>(tab[blockIdx.y]);
+    T* b = buf + blockIdx.y * n;
+    if (save) b[i] = f[i];
+    else f[i] = b[i];
+}
+
 // state (hi, lo) <-> a flat buffer; lo may be null (FP64 form)
 template <typename T>
 __global__ void state_copy_kernel(T* __restrict__ dst_hi, T* __restrict__ dst_lo, const T* __restrict__ src_hi,

@@ -29,6 +29,8 @@ enum {
     RB1, RB2, RB3, FB1, FB2, FB3, HF1, HF2, HF3, bHE1, bHE2, bHE3, NSLOT
 };
 static_assert(NSLOT <= kMaxSlots, "slot table too small");
+// slots a recorded step leaves for its reverse (the forward step's and the recorded intermediates)
+constexpr int kRecSlots = G1;
 // spectral slots
 enum { S1 = 0, S2, S3, H1, H2, H3, NSPEC_FWD, SA1 = NSPEC_FWD, SA2, SA3, NSPEC };
 
@@ -82,6 +84,7 @@ struct sgspm_ctx {
     int rec_K = 0;
     void* d_ckpt = nullptr;            // checkpoints: [seg][hi/lo][3][ncell]
     void* d_seg = nullptr;             // states of one segment: [K][hi/lo][3][ncell]
+    void* d_rec = nullptr;             // recorded slots of one segment: [K][kRecSlots][ncell] (hi), or null
     void* d_final = nullptr;           // m(T) while the reverse sweep runs
     double* d_apart = nullptr;         // alpha gradient block partials
     double* d_alpha_b = nullptr;       // alpha gradient per film
@@ -141,6 +144,10 @@ struct sgspm_ctx {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t adj_graph = nullptr;       // reverse step: forward transform, recording step, adjoint step
     cudaGraphExec_t adj_gexec = nullptr;
+    cudaGraph_t radj_graph = nullptr;      // reverse step from restored recordings: adjoint step only
+    cudaGraphExec_t radj_gexec = nullptr;
+    cudaGraph_t rrec_graph = nullptr;      // segment replay: recording step
+    cudaGraphExec_t rrec_gexec = nullptr;
     bool have_m = false;
     bool forcing = false;
     long long steps = 0;
@@ -961,10 +968,16 @@ static int drop_graph(sgspm_ctx* ctx) {
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     if (ctx->adj_gexec) cudaGraphExecDestroy(ctx->adj_gexec);
     if (ctx->adj_graph) cudaGraphDestroy(ctx->adj_graph);
+    for (cudaGraphExec_t* e : {&ctx->radj_gexec, &ctx->rrec_gexec})
+        if (*e) cudaGraphExecDestroy(*e);
+    for (cudaGraph_t* g : {&ctx->radj_graph, &ctx->rrec_graph})
+        if (*g) cudaGraphDestroy(*g);
     ctx->gexec = nullptr;
     ctx->graph = nullptr;
     ctx->adj_gexec = nullptr;
     ctx->adj_graph = nullptr;
+    ctx->radj_gexec = ctx->rrec_gexec = nullptr;
+    ctx->radj_graph = ctx->rrec_graph = nullptr;
     ctx->p_stale = true;
     return SGSPM_OK;
 }
@@ -987,6 +1000,23 @@ static int capture_reverse(sgspm_ctx* ctx) {
     if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     ctx->adj_graph = g;
     CK(cudaGraphInstantiate(&ctx->adj_gexec, g, 0));
+    return SGSPM_OK;
+}
+
+// One program captured into a graph (the reverse sweep's recording and adjoint steps).
+static int capture_prog(sgspm_ctx* ctx, const std::vector<Launch>& prog, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+    if (*exec) return SGSPM_OK;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = run_prog(ctx, prog, ctx->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, SGSPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    *graph = g;
+    CK(cudaGraphInstantiate(exec, g, 0));
     return SGSPM_OK;
 }
 
@@ -1591,7 +1621,7 @@ static void release(sgspm_ctx* ctx) {
     }
     for (int i = 0; i < kMaxSpec; ++i)
         if (ctx->d_spec[i]) cudaFree(ctx->d_spec[i]);
-    void* more[] = {ctx->d_tab, ctx->d_tab_lo, ctx->d_tab_spec, ctx->d_ckpt, ctx->d_seg, ctx->d_final, ctx->d_apart,
+    void* more[] = {ctx->d_tab, ctx->d_tab_lo, ctx->d_tab_spec, ctx->d_ckpt, ctx->d_seg, ctx->d_rec, ctx->d_final, ctx->d_apart,
                     ctx->d_alpha_b, ctx->d_ycache, ctx->d_tc_test, ctx->d_pph, ctx->d_pit, ctx->d_pfi, ctx->d_pctl};
     for (void* p : more)
         if (p) cudaFree(p);
@@ -1757,9 +1787,16 @@ static int rec_alloc_t(sgspm_ctx* ctx, long long nseg, int K) {
     }
     if (ctx->d_ckpt) cudaFree(ctx->d_ckpt);
     if (ctx->d_seg) cudaFree(ctx->d_seg);
-    ctx->d_ckpt = ctx->d_seg = nullptr;
+    if (ctx->d_rec) cudaFree(ctx->d_rec);
+    ctx->d_ckpt = ctx->d_seg = ctx->d_rec = nullptr;
     CK(cudaMalloc(&ctx->d_ckpt, (size_t)nseg * 6 * cell));
     CK(cudaMalloc(&ctx->d_seg, (size_t)K * 6 * cell));
+    // the recorded slots of every step of a segment, so that the reverse sweep need not run each
+    // step's recording again; without the memory it falls back to recomputing them
+    if (cudaMalloc(&ctx->d_rec, (size_t)K * kRecSlots * cell) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->d_rec = nullptr;
+    }
     return SGSPM_OK;
 }
 
@@ -1832,6 +1869,36 @@ static int grad_t(sgspm_ctx* ctx, const void* dL_dmT, int dtype, void* dL_dhe, d
         if ((rc = state_io<T>(ctx, ck + sgi * per, false))) return rc;
         if ((rc = run_prog(ctx, ctx->fwd_prog, ctx->stream))) return rc;
         const bool graphs = !(ctx->flags & SGSPM_NO_GRAPH);
+        if (ctx->d_rec) {
+            // replay the segment with the recording step and keep every step's recorded slots;
+            // the reverse of a step then restores them and runs the adjoint step alone
+            T* rb = (T*)ctx->d_rec;
+            const long long rper = (long long)kRecSlots * n;
+            const dim3 sgrid(nb, kRecSlots);
+            if (graphs && (rc = capture_prog(ctx, ctx->rec_prog, &ctx->rrec_graph, &ctx->rrec_gexec))) return rc;
+            if (graphs && (rc = capture_prog(ctx, ctx->adj_prog, &ctx->radj_graph, &ctx->radj_gexec))) return rc;
+            for (long long j = 0; j < L; ++j) {
+                if (graphs) CK(cudaGraphLaunch(ctx->rrec_gexec, ctx->stream));
+                else if ((rc = run_prog(ctx, ctx->rec_prog, ctx->stream))) return rc;
+                slots_io_kernel<T><<<sgrid, 256, 0, ctx->stream>>>(rb + j * rper, ctx->d_tab, n, 1);
+                CK(cudaGetLastError());
+                if (j + 1 == L) break;
+                // the next state is m^{n+1} (MN1..3, hi and lo), with its forward transform
+                for (int a = 0; a < 3; ++a)
+                    state_copy_kernel<T><<<nb, 256, 0, ctx->stream>>>((T*)ctx->d_field[M1 + a], (T*)ctx->d_flo[M1 + a],
+                                                                      (const T*)ctx->d_field[MN1 + a],
+                                                                      (const T*)ctx->d_flo[MN1 + a], n);
+                CK(cudaGetLastError());
+                if ((rc = run_prog(ctx, ctx->fwd_prog, ctx->stream))) return rc;
+            }
+            for (long long j = L - 1; j >= 0; --j) {
+                slots_io_kernel<T><<<sgrid, 256, 0, ctx->stream>>>(rb + j * rper, ctx->d_tab, n, 0);
+                CK(cudaGetLastError());
+                if (graphs) CK(cudaGraphLaunch(ctx->radj_gexec, ctx->stream));
+                else if ((rc = run_prog(ctx, ctx->adj_prog, ctx->stream))) return rc;
+            }
+            continue;
+        }
         if (graphs && !ctx->gexec && (rc = capture_step(ctx))) return rc;
         for (long long j = 0; j < L; ++j) {
             if ((rc = state_io<T>(ctx, sg + j * per, true))) return rc;
