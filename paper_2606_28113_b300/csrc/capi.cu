@@ -739,19 +739,20 @@ static void build_adjoint(sgspm_ctx* ctx) {
         Y.y.in_mask = mask;
         for (int i = 0; i < 3; ++i) Y.y.in_spec[i] = SA1 + i;
         P.push_back(Y);
+        // the inverse transforms add h_s of the adjoint input straight into the state adjoints
         Launch Hs = blank(0);
         Hs.xz.n_rhs = 3;
         Hs.xz.rhs_dct = 0;
+        Hs.xz.rhs_hs_add = 1;
         for (int i = 0; i < 3; ++i) {
             Hs.xz.rhs_comp[i] = i;
             Hs.xz.rhs_h[i] = H1 + i;
-            Hs.xz.rhs_hs_store[i] = HF1 + i;
+            Hs.xz.rhs_hs_store[i] = sb[i];
         }
         Hs.xz.state[0] = M1;
         Hs.xz.state[1] = M2;
         Hs.xz.state[2] = M3;
         P.push_back(Hs);
-        ew(0, {sb[0], sb[1], sb[2]}, {HF1, HF2, HF3});
     };
     auto gs = [&](int ub, int base_b, int p, int p_b, int q, int q_b, int r, int r_b, int s_, int s_b) {
         Launch L = blank(4);

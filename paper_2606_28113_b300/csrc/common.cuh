@@ -170,6 +170,7 @@ struct XZProg {
     int rhs_h[3];          // spectral slot of H_a to invert for h_s,a (-1: no stray term)
     int rhs_out[3];        // real slot receiving DCT_xz(r_a)
     int rhs_hs_store[3];   // real slot receiving h_s,a (-1: none)
+    int rhs_hs_add;        // 1: h_s,a is added to that slot instead of stored (adjoint accumulators)
     int state[3];          // real slots of the state (m1, m2, m3) at which f is evaluated
     int damp;              // 0: scale = dt; 1: scale = alpha dt
     int rhs_dct;           // 0: only invert h_s (energy), no rhs / DCT

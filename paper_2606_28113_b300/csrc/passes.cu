@@ -226,6 +226,12 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
                 }
             }
         };
+        auto add_slab = [&](T* __restrict__ f, const T* sl) {   // f += slab (each cell once)
+            for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) {
+                const int z = idx / nx, x = idx - z * nx;
+                f[cell_of(z, x)] += sl[idx];
+            }
+        };
         const bool zreg = z_in_registers(nz);
         const T* Cz = sdt;                                       // DCT-II  C[k][n]
         const T* Czi = sdt + nz * nz;                            // inverse Ci[n][k]
@@ -352,7 +358,10 @@ __device__ __forceinline__ void xz_item(const Dev<T> d, const int4 wi, const XZP
                 for (int idx = threadIdx.x; idx < nxz; idx += blockDim.x) h[idx] = T(0);
             }
             __syncthreads();
-            if (MODE == 0 && pg.rhs_hs_store[ci] >= 0) store_slab(d.field[pg.rhs_hs_store[ci]], h);
+            if (MODE == 0 && pg.rhs_hs_store[ci] >= 0) {
+                if (pg.rhs_hs_add) add_slab(d.field[pg.rhs_hs_store[ci]], h);
+                else store_slab(d.field[pg.rhs_hs_store[ci]], h);
+            }
             if (MODE == 0 && !pg.rhs_dct) { __syncthreads(); continue; }
             // r_a = scale * (f_a + eps Delta_h m_a),  f_a = -Q (m_a - (m.u) u_a) + h_s,a + h_e,a
             if (MODE != 0 || pg.rhs_copy[ci] < 0) {
