@@ -1124,14 +1124,26 @@ __device__ __forceinline__ void y_stray_warp_item(const Dev<T> d, const int4 wi,
     V* inb = scr0 + LINES * P;                                       // [3][lines][LI]
     T* kbuf = reinterpret_cast<T*>(inb + 3 * LINES * LI);            // [3 NOUT][lines][HyP]
     stage_async(stw, d.tw + d.plans[F.plan_py].tw, P);
-    cp_async_commit();
-    cp_async_wait(0);
-    pdl_wait();
-    // ---- asynchronous staging: group b = input component b and the table lines of (o, b)
-    const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx0;
+    // the Newell table lines of the pairs (o, b) are constant: their copies are issued with the
+    // twiddles, before the wait for the previous pass, so that they overlap its tail
     const T* kt = d.ktab + F.off_ktab;
     constexpr int KCH = 16 / (int)sizeof(T);   // table elements per 16-byte piece
     const int nkch = tn * HyP / KCH;
+#pragma unroll 1
+    for (int b = 0; b < 3; ++b) {
+        if (!(pg.in_mask & (1 << b))) continue;
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            const int cc = pair_idx(pg.slot[o], b);
+            const T* src = kt + (((long long)cc * Hz + kzr) * Kx + kx0) * HyP;
+            T* kd = kbuf + (o * 3 + b) * LINES * HyP;
+            for (int i = threadIdx.x; i < nkch; i += blockDim.x) cp_async_16(kd + i * KCH, src + i * KCH);
+        }
+    }
+    cp_async_commit();   // group 0: twiddles and table lines (complete before component 0 is used)
+    pdl_wait();
+    // ---- asynchronous staging: group 1 + b = the fresh input component b (spectrum tile)
+    const long long line0 = F.off_spec + (long long)kz * ny * Kx + kx0;
 #pragma unroll 1
     for (int b = 0; b < 3; ++b) {
         if (pg.in_mask & (1 << b)) {
@@ -1142,13 +1154,6 @@ __device__ __forceinline__ void y_stray_warp_item(const Dev<T> d, const int4 wi,
             for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
                 const int y = idx / tn, t = idx - y * tn;
                 cp_async<(int)sizeof(V)>(dst + t * LI + y, Sb + (long long)y * Kx + t);
-            }
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                const int cc = pair_idx(pg.slot[o], b);
-                const T* src = kt + (((long long)cc * Hz + kzr) * Kx + kx0) * HyP;
-                T* kd = kbuf + (o * 3 + b) * LINES * HyP;
-                for (int i = threadIdx.x; i < nkch; i += blockDim.x) cp_async_16(kd + i * KCH, src + i * KCH);
             }
         }
         cp_async_commit();
