@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(kThreads) adj_f_kernel(Dev<T> d, const int4* _
 struct AdjEw {
     int n;
     int mode;               // 0 add, 1 zero, 2 copy
-    int dst[12];
-    int src[12];
+    int dst[16];
+    int src[16];
 };
 
 template <typename T>

@@ -26,7 +26,7 @@ enum {
     M1 = 0, M2, M3, A1, A2, A3, B1, B2, E3N, E1S, E3SS, D1, D2, D3, HS1, HS2, HS3, NSLOT_FWD,
     D2N = NSLOT_FWD, D2S, D2SS, V1, V2, V3, MN1, MN2, MN3, ERS1, ERS2, ERS3,
     G1, G2, G3, bM1, bM2, bM3, bA1, bA2, bA3, bB1, bB2, bD2N, bE3N, bE1S, bD2S, bE3SS, bD2SS,
-    RB1, RB2, RB3, FB1, FB2, FB3, HF1, HF2, HF3, bHE1, bHE2, bHE3, NSLOT
+    RB1, RB2, RB3, FB1, FB2, FB3, bHE1, bHE2, bHE3, NSLOT
 };
 static_assert(NSLOT <= kMaxSlots, "slot table too small");
 // slots a recorded step leaves for its reverse (the forward step's and the recorded intermediates)
@@ -675,10 +675,10 @@ static void build_adjoint(sgspm_ctx* ctx) {
         return L;
     };
     auto ew = [&](int mode, const std::vector<int>& dst, const std::vector<int>& src) {
-        for (size_t i0 = 0; i0 < dst.size(); i0 += 12) {
+        for (size_t i0 = 0; i0 < dst.size(); i0 += 16) {
             Launch L = blank(6);
             L.ew.mode = mode;
-            L.ew.n = (int)std::min<size_t>(12, dst.size() - i0);
+            L.ew.n = (int)std::min<size_t>(16, dst.size() - i0);
             for (int k = 0; k < L.ew.n; ++k) {
                 L.ew.dst[k] = dst[i0 + k];
                 L.ew.src[k] = src.empty() ? 0 : src[i0 + k];
