@@ -438,7 +438,10 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": bpc * ncell, "launch_ms": dom_ms,
                 "kernel_share_of_step": per_type[dom_type] / total,
                 "traffic": NCU_TRAFFIC.get(dom_kind) if args.form == "fp32" else None,
-                "traffic_unit": "bytes per launch (ncu dram read + write, cold caches)"}
+                "traffic_unit": "bytes per launch (ncu dram read + write, cold caches)",
+                "traffic_source": ("profiles/passes_film256x256x8_fp32.md: ncu --set full of the right-hand-side "
+                                   "launches of the 512-thread slab kernel (one capture, mean over a step's six "
+                                   "launches)") if args.form == "fp32" and NCU_TRAFFIC.get(dom_kind) else None}
     # whole-step algorithmic fraction (292 B per cell-step, FP32)
     step_frac = 292.0 * value / world / (hbm * 1e9) if hbm else None
 
