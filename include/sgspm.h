@@ -307,7 +307,7 @@ const char* sgspm_noalloc_last_error(void);
  */
 int sgspm_fp64_fma_peak(double* gflops);
 
-/* ABI version (major*100 + minor). */
+/* ABI version (major*100 + minor); 102 added sgspm_xz_threads and sgspm_set_packing_threads. */
 int sgspm_version(void);
 
 #ifdef __cplusplus

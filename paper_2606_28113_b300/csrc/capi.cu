@@ -1941,7 +1941,7 @@ static int grad_t(sgspm_ctx* ctx, const void* dL_dmT, int dtype, void* dL_dhe, d
 
 extern "C" {
 
-int sgspm_version(void) { return 101; }
+int sgspm_version(void) { return 102; }
 
 const char* sgspm_last_error(sgspm_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 

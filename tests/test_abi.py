@@ -27,7 +27,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_version():
-    assert sgspm.lib().sgspm_version() == 101
+    assert sgspm.lib().sgspm_version() == 102
 
 
 def _create(grid, eps=0.1, Q=0.1, alpha=0.1, dt=0.01, u=(1.0, 0.0, 0.0)):
